@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Benchmark: PW momentum advection (MONC, Sec. 2.1) on GB300.
+
+Headline step: one FP64 forward pass (su, sv, sw from u, v, w) over the
+2048 x 2048 x 64 grid (268M points, 12.9 GB of fields), inputs resident in
+HBM, timed with CUDA events on the launching stream.  Also reported on the
+same line: the end-to-end rate through the host-buffer C-ABI call, the
+roofline of the forward kernel, the FP32 / FP16-storage variants with their
+error against the FP64 result, the adjoint, the ensemble, the GPU clocks
+during the timed region, and the CPU oracle on this machine's host cores.
+
+``--impl reference`` times the CPU oracle (test infrastructure; the only
+other place this script runs it is the cpu_baseline leg).
+
+Multi-GPU: the grid does not need more than one GPU, so ``--gpus N`` runs N
+independent replicas (weak scaling, no collective on the data path); rank 0
+prints the whole-job rate over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "advection grid points/s (FP64 vs FP32/FP16-storage) and % of HBM roofline"
+UNIT = "points/s"
+SHAPE = (2048, 2048, 64)
+FLOP_PER_POINT = 53           # the paper's count for su, sv, sw (Sec. 2.3)
+BYTES_PER_POINT = {"f64": 48, "f32": 24, "f16s": 12}       # 3 fields in + 3 out
+ADJ_BYTES_PER_POINT = {"f64": 72, "f32": 36}                # 6 in + 3 out
+ADJ_SHAPE = (1024, 1024, 128)
+FP64_DFMA_PER_CLK_PER_SM = 2   # see the design doc (measured throughput probe)
+N_SM = 152
+
+
+# ----------------------------------------------------------------- helpers
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def profile_traffic(kernel_name, src_hash):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_name}_2048x2048x64.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha1") != src_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def kernel_source_hash():
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2010_01545_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# ----------------------------------------------------------------- oracle legs
+def oracle_sample_rate(winds, grid, planes, repeats=1):
+    import oracle
+    c = oracle.coefficients(grid)
+    sub = [np.ascontiguousarray(a[: planes + 2]) for a in winds]   # planes + x-halo
+    best = None
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        oracle.forward(*sub, c, i_range=(1, planes + 1))
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return planes * SHAPE[1] * SHAPE[2] / best, best
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import workload
+    grid = workload.vertical_grid(SHAPE[2])
+    planes = 128
+    winds = [workload.wind_field(planes + 2, SHAPE[1], SHAPE[2], f) for f in range(3)]
+    import oracle
+    c = oracle.coefficients(grid)
+    for _ in range(args.warmup):
+        oracle.forward(*winds, c, i_range=(1, planes + 1))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.forward(*winds, c, i_range=(1, planes + 1))
+    dt = time.perf_counter() - t0
+    pts = planes * SHAPE[1] * SHAPE[2]
+    value = pts * args.steps / dt
+    sample = (f"{planes} x-planes ({pts} points) of the 2048x2048x64 FP64 forward per step, "
+              "single-threaded plain C oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "pw_advection_fwd_2048x2048x64_f64",
+                                            "sample_points_per_step": pts},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- GPU legs
+def time_calls(fn, steps, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def normwise_errors(got, ref):
+    import torch
+    out = []
+    for g, r in zip(got, ref):
+        g = g.to(torch.float64)
+        d = g - r
+        m = torch.max(torch.abs(r)).item()
+        out.append({"max_rel": torch.max(torch.abs(d)).item() / m,
+                    "rms_rel": (torch.linalg.vector_norm(d) / torch.linalg.vector_norm(r)).item()})
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-variants", action="store_true", help="headline only")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+
+    import workload
+    from paper_2010_01545_gb300 import build, torch_api
+    build.build()
+
+    grid = workload.vertical_grid(SHAPE[2])
+    coeffs = torch_api.coefficients_from_grid(grid)
+    n_pts = SHAPE[0] * SHAPE[1] * SHAPE[2]
+    winds = workload.winds(*SHAPE, seed=workload.DEFAULT_SEED + rank)
+    op = torch_api.Advect(*SHAPE, coeffs, "f64")
+    d_in = [torch.from_numpy(a).cuda() for a in winds]
+    d_out = [op.empty() for _ in range(3)]
+
+    def step():
+        op.forward(*d_in, out=d_out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        secs = time_calls(step, args.steps, stream)
+    if world > 1:
+        t = torch.tensor([secs], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = t.item()
+    value = world * n_pts * args.steps / secs
+    per_launch = secs / args.steps
+    fwd_name = op.kernel_name()
+
+    hbm_gbs, sm_max_mhz, peak_kind = peaks()
+    fp64_peak_gflops = 2 * FP64_DFMA_PER_CLK_PER_SM * N_SM * sm_max_mhz * 1e6 / 1e9
+    achieved_gflops = FLOP_PER_POINT * n_pts / per_launch / 1e9
+    achieved_gbs = BYTES_PER_POINT["f64"] * n_pts / per_launch / 1e9
+    src_hash = kernel_source_hash()
+    traffic = profile_traffic(fwd_name, src_hash)
+    roofline = {"bound": "alu", "achieved": achieved_gflops, "peak": fp64_peak_gflops,
+                "unit": "GFLOP/s", "frac": achieved_gflops / fp64_peak_gflops, "traffic": traffic,
+                "kernel": fwd_name, "peak_kind": "FP64 pipe: 2 DFMA/clk/SM x 152 SM x max SM clock",
+                "hbm": {"achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s",
+                        "frac": achieved_gbs / hbm_gbs, "peak_kind": peak_kind}}
+
+    # end to end through the host-buffer C-ABI call (pinned host memory)
+    h_in = [torch.from_numpy(a).pin_memory() for a in winds]
+    h_out = [torch.empty(SHAPE, dtype=torch.float64).pin_memory() for _ in range(3)]
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        op.forward_host(*h_in, h_out)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        op.forward_host(*h_in, h_out)
+    e2e_secs = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": world * n_pts / e2e_secs, "unit": UNIT,
+           "h2d_bytes_per_step": 3 * n_pts * 8, "d2h_bytes_per_step": 3 * n_pts * 8,
+           "ms_per_step": 1e3 * e2e_secs}
+    del h_in, h_out
+
+    ref_out = [t.clone() for t in d_out]
+    variants = {}
+    if not args.no_variants:
+        variants = run_variants(args, torch, torch_api, workload, winds, coeffs, ref_out, stream,
+                                hbm_gbs, grid)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle  # noqa: F401  (CPU baseline leg)
+        rate, dt = oracle_sample_rate(winds, grid, SHAPE[0] - 2)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"FP64 forward over {SHAPE[0] - 2} of the 2048 x-planes of the same grid "
+                         f"({dt:.1f} s, single-threaded plain C, -O2 -ffp-contract=off)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * per_launch, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "pw_advection_fwd_2048x2048x64_f64", "nx": SHAPE[0],
+                           "ny": SHAPE[1], "nz": SHAPE[2], "points": n_pts,
+                           "l2": "inputs (6.4 GB) larger than L2; no flush",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps,
+                "clocks": clk.summary(), "cpu_baseline": cpu, "variants": variants,
+                "kernel_source": src_hash}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_variants(args, torch, torch_api, workload, winds, coeffs, ref_out, stream, hbm_gbs, grid):
+    out = {}
+    n_pts = SHAPE[0] * SHAPE[1] * SHAPE[2]
+    steps = max(3, min(args.steps, 10))
+    # FP32 storage + arithmetic
+    op32 = torch_api.Advect(*SHAPE, coeffs, "f32")
+    d32 = [torch.from_numpy(a).to("cuda", torch.float32) for a in winds]
+    o32 = [op32.empty() for _ in range(3)]
+    for _ in range(args.warmup):
+        op32.forward(*d32, out=o32)
+    secs = time_calls(lambda: op32.forward(*d32, out=o32), steps, stream) / steps
+    errs = normwise_errors(o32, ref_out)
+    out["f32"] = {"value": n_pts / secs, "unit": UNIT, "ms": 1e3 * secs, "kernel": op32.kernel_name(),
+                  "hbm_frac": BYTES_PER_POINT["f32"] * n_pts / secs / 1e9 / hbm_gbs,
+                  "error_vs_f64": dict(zip(("su", "sv", "sw"), errs))}
+    del d32, o32, op32
+    # FP16 storage with per-field power-of-two scales
+    op16 = torch_api.Advect(*SHAPE, coeffs, "f16s")
+    s_in = [float(2.0 ** np.ceil(np.log2(np.max(np.abs(a))))) for a in winds]
+    s_out = op16.output_scales(s_in)
+    d16 = [(torch.from_numpy(a).cuda() / s).to(torch.float16) for a, s in zip(winds, s_in)]
+    o16 = [op16.empty() for _ in range(3)]
+    sc = s_in + s_out
+    for _ in range(args.warmup):
+        op16.forward(*d16, out=o16, scales=sc)
+    secs = time_calls(lambda: op16.forward(*d16, out=o16, scales=sc), steps, stream) / steps
+    errs = normwise_errors([o.to(torch.float64) * s for o, s in zip(o16, s_out)], ref_out)
+    out["f16s"] = {"value": n_pts / secs, "unit": UNIT, "ms": 1e3 * secs, "kernel": op16.kernel_name(),
+                   "hbm_frac": BYTES_PER_POINT["f16s"] * n_pts / secs / 1e9 / hbm_gbs,
+                   "error_vs_f64": dict(zip(("su", "sv", "sw"), errs)),
+                   "note": "error includes the fp16 quantisation of the inputs"}
+    del d16, o16, op16
+    torch.cuda.empty_cache()
+    # adjoint on the 1024 x 1024 x 128 differentiation grid
+    agrid = workload.vertical_grid(ADJ_SHAPE[2])
+    acoef = torch_api.coefficients_from_grid(agrid)
+    an = ADJ_SHAPE[0] * ADJ_SHAPE[1] * ADJ_SHAPE[2]
+    for name, tdt in (("f64", torch.float64), ("f32", torch.float32)):
+        opa = torch_api.Advect(*ADJ_SHAPE, acoef, name)
+        x = [torch.from_numpy(a).to("cuda", tdt) for a in workload.winds(*ADJ_SHAPE, seed=7)]
+        lam = [torch.from_numpy(a).to("cuda", tdt) for a in workload.cotangents(*ADJ_SHAPE, seed=8)]
+        g = [opa.empty() for _ in range(3)]
+        for _ in range(args.warmup):
+            opa.adjoint(*x, *lam, out=g)
+        secs = time_calls(lambda: opa.adjoint(*x, *lam, out=g), steps, stream) / steps
+        out[f"adjoint_{name}_1024x1024x128"] = {
+            "value": an / secs, "unit": UNIT, "ms": 1e3 * secs, "kernel": opa.kernel_name(True),
+            "hbm_frac": ADJ_BYTES_PER_POINT[name] * an / secs / 1e9 / hbm_gbs}
+        del x, lam, g, opa
+        torch.cuda.empty_cache()
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,41 @@
+// kernels.h -- host-side launchers of the advection kernels (internal API).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace advect {
+
+// Element type codes (same values as advect_dtype).
+enum Dtype { kF64 = 0, kF32 = 1, kF16S = 2 };
+
+struct FwdArgs {
+  const void *u, *v, *w;
+  void *su, *sv, *sw;
+  Shape s;
+  Coeffs c;
+  Scales sc;
+  int f64_levels;  // F32/F16S: levels 1..f64_levels use binary64 vertical terms
+  int i0, i1;      // x-planes [i0, i1) are computed (the others are untouched)
+};
+
+struct AdjArgs {
+  const void *u, *v, *w, *dsu, *dsv, *dsw;
+  void *du, *dv, *dw;
+  Shape s;
+  Coeffs c;
+};
+
+// Plane-sweep tile configuration (see fwd_sweep.cu).
+struct SweepCfg {
+  int ty;       // rows (y) per CTA
+  int lx;       // x-planes per CTA
+  int threads;  // threads per CTA
+};
+
+// One thread per grid point, plain loads: any shape and alignment.
+cudaError_t launch_fwd_point(int dtype, const FwdArgs& a, cudaStream_t st);
+cudaError_t launch_adj_point(int dtype, const AdjArgs& a, cudaStream_t st);
+
+}  // namespace advect

@@ -1,0 +1,104 @@
+"""Parity at the benchmark's full sizes, in the same launch configuration.
+
+The 2048 x 2048 x 64 forward (268M points) runs through the same context
+creation as bench.py; the oracle evaluates a sample of points one by one
+(every boundary class plus random interior points).  The 1024 x 1024 x 128
+adjoint is checked by properties that hold at any size: the dot-product
+identity and central differences at 64 random probes.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workload
+from gpu_util import dev, host, make_op
+
+pytestmark = pytest.mark.gpu
+
+
+def sample_indices(shape, n_random, seed):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    pts = [(int(rng.integers(nx)), int(rng.integers(ny)), int(rng.integers(nz))) for _ in range(n_random)]
+    for i in (0, 1, nx - 1):
+        for j in (0, ny - 1, ny // 2):
+            for k in (0, 1, 2, nz - 2, nz - 1):
+                pts.append((i, j, k))
+    return np.array([(i * ny + j) * nz + k for i, j, k in pts], dtype=np.int64)
+
+
+@pytest.fixture(scope="module")
+def big_winds():
+    return workload.winds(2048, 2048, 64, seed=workload.DEFAULT_SEED)
+
+
+def _check_sample(outs, winds, grid, shape, tol, seed):
+    idx = sample_indices(shape, 20000, seed)
+    ref = oracle.forward_points(*winds, oracle.coefficients(grid), idx)
+    for f in range(3):
+        g = outs[f].reshape(-1)[torch.from_numpy(idx).cuda()].to(torch.float64).cpu().numpy()
+        r = ref[:, f]
+        err = np.max(np.abs(g - r)) / np.max(np.abs(r))
+        assert err <= tol, f"field {f}: sampled normwise error {err:.3e}"
+
+
+def test_forward_f64_2048x2048x64_sampled(big_winds):
+    shape = (2048, 2048, 64)
+    op, grid = make_op(shape, "f64")
+    outs = op.forward(*(dev(a) for a in big_winds))
+    torch.cuda.synchronize()
+    _check_sample(outs, big_winds, grid, shape, 1e-12, 1)
+    del outs
+    torch.cuda.empty_cache()
+
+
+def test_forward_f32_2048x2048x64_sampled(big_winds):
+    shape = (2048, 2048, 64)
+    op, grid = make_op(shape, "f32")
+    w32 = [a.astype(np.float32) for a in big_winds]
+    outs = op.forward(*(torch.from_numpy(a).cuda() for a in w32))
+    torch.cuda.synchronize()
+    _check_sample(outs, [a.astype(np.float64) for a in w32], grid, shape, 2e-6, 2)
+    del outs
+    torch.cuda.empty_cache()
+
+
+def test_adjoint_f64_1024x1024x128_dot_product_and_probes():
+    shape = (1024, 1024, 128)
+    op, _ = make_op(shape, "f64")
+    x = [dev(a) for a in workload.winds(*shape, seed=41)]
+    d = [dev(a) for a in workload.cotangents(*shape, seed=42)]
+    lam = [dev(a) for a in workload.cotangents(*shape, seed=43)]
+    h = 2.0 ** -10
+    fp = op.forward(*(a + h * b for a, b in zip(x, d)))
+    fm = op.forward(*(a - h * b for a, b in zip(x, d)))
+    jd = [(a - b) / (2 * h) for a, b in zip(fp, fm)]
+    del fp, fm
+    jt = op.adjoint(*x, *lam)
+    lhs = sum(torch.sum(a * b).item() for a, b in zip(jd, lam))
+    rhs = sum(torch.sum(a * b).item() for a, b in zip(d, jt))
+    mag = sum(torch.sum(torch.abs(a * b)).item() for a, b in zip(d, jt))
+    assert abs(lhs - rhs) <= 1e-10 * mag
+    del jd, d
+    jt_h = [host(t) for t in jt]
+    rng = np.random.default_rng(44)
+    eps = 1e-6
+    out_p = op.forward(*x)
+    for _ in range(64):
+        f = int(rng.integers(3))
+        p = tuple(int(rng.integers(n)) for n in shape)
+        keep = x[f][p].item()
+        x[f][p] = keep + eps
+        op.forward(*x, out=out_p)
+        # only the 3x3x3 neighbourhood of p changes
+        sl = tuple(slice(max(c - 1, 0), c + 2) for c in p)
+        plus = [o[sl].clone() for o in out_p]
+        x[f][p] = keep - eps
+        op.forward(*x, out=out_p)
+        minus = [o[sl].clone() for o in out_p]
+        x[f][p] = keep
+        fd = sum(torch.sum((a - b) * l[sl]).item() for a, b, l in zip(plus, minus, lam)) / (2 * eps)
+        # probes away from the periodic seams see their whole neighbourhood
+        if all(0 < c < n - 1 for c, n in zip(p[:2], shape[:2])):
+            assert abs(fd - jt_h[f][p]) <= 1e-7 * (1 + abs(jt_h[f][p])), (f, p, fd, jt_h[f][p])
