@@ -21,8 +21,8 @@
  *
  * Element types (advect_dtype): ADVECT_F64 stores and computes in binary64;
  * ADVECT_F32 stores and computes in binary32 (coefficient tables kept in
- * binary64, vertical terms near the surface in binary64 -- see
- * advect_set_f64_levels); ADVECT_F16S stores binary16 values x/s with a
+ * binary64; optionally the vertical terms of the lowest levels in binary64 --
+ * see advect_set_f64_levels); ADVECT_F16S stores binary16 values x/s with a
  * power-of-two scale s per field and computes in binary32 (the paper's
  * future-work precision trade-off, Sec. 6).
  *
@@ -160,8 +160,9 @@ advect_status advect_f16s_output_scales(const advect_ctx *ctx, const float *in, 
 /*
  * ADVECT_F32 / ADVECT_F16S: number of levels k = 1..n whose vertical terms
  * are evaluated in binary64 with the binary64 tables (near-surface levels,
- * where dz is smallest and the vertical fluxes largest).  0 disables; the
- * default is 2.  EINVAL if n < 0.
+ * where dz is smallest and the vertical fluxes largest).  0 (the default)
+ * disables: on GB300 binary64 runs at 1/74 of the binary32 rate, so even two
+ * such levels more than double the kernel time.  EINVAL if n < 0.
  */
 advect_status advect_set_f64_levels(advect_ctx *ctx, int n);
 

@@ -38,7 +38,7 @@ struct advect_ctx {
   bool ensemble = false;
   advect_dtype dtype = ADVECT_F64;
   int device = 0;
-  int f64_levels = 2;
+  int f64_levels = 0;
   int* d_flag = nullptr;  // device error flag (non-zero: a bounded wait gave up)
   std::vector<advect::Member> members;
   std::string fwd_name, adj_name;

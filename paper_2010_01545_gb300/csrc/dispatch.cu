@@ -1,18 +1,81 @@
 // dispatch.cu -- kernel selection, context resources.
 #include <cuda_runtime.h>
 
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+
 #include "ctx.h"
 
 namespace advect {
 
+namespace {
+
+int elem_of(int dtype) { return dtype == kF64 ? 8 : (dtype == kF32 ? 4 : 2); }
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+}  // namespace
+
+// Default plane-sweep tile for a column height and element size; ty = 0 when
+// the sweep kernel cannot take this shape.
+SweepCfg default_sweep(int nz, int elem) {
+  SweepCfg c{0, 64, 4};
+  const int P = sweep_vec(elem);
+  if (nz % P || (nz * elem) % 16) return c;
+  const int kb = nz / P;
+  if (kb > 256) return c;
+  // ~128 threads per CTA: at ~150-170 registers per thread three CTAs fit
+  // per SM, which hides latency better than one 256-thread CTA (measured
+  // on the 2048 x 2048 x 64 grid).
+  int ty = kb >= 128 ? 1 : 128 / kb;
+  while (ty > 1 && (ty * kb) % 32) --ty;
+  if ((ty * kb) % 32) {
+    ty = 256 / kb;
+    while (ty > 1 && (ty * kb) % 32) --ty;
+    if ((ty * kb) % 32) return c;
+  }
+  c.ty = ty;
+  // a deep ring keeps enough bytes in flight to cover HBM latency
+  c.nb = elem == 2 ? 16 : 8;
+  while (c.nb > 4 && sweep_smem_bytes(nz, elem, c) > 72 * 1024) --c.nb;
+  while (c.ty > 1 && sweep_smem_bytes(nz, elem, c) > 220 * 1024) {
+    int t = c.ty - 1;
+    while (t > 1 && (t * kb) % 32) --t;
+    if ((t * kb) % 32) break;
+    c.ty = t;
+  }
+  if (sweep_smem_bytes(nz, elem, c) > 220 * 1024 || (uint64_t)3 * (c.ty + 2) * nz * elem >= (1u << 20))
+    c.ty = 0;
+  return c;
+}
+
+// ADVECT_SWEEP="ty,lx,nb" overrides the plane-sweep tile (ignored unless valid).
+static void sweep_override(SweepCfg& c, int nz, int elem) {
+  const char* s = getenv("ADVECT_SWEEP");
+  if (!s || c.ty == 0) return;
+  SweepCfg o{0, 0, 0};
+  if (sscanf(s, "%d,%d,%d", &o.ty, &o.lx, &o.nb) != 3) return;
+  const int kb = nz / sweep_vec(elem);
+  if (o.ty < 1 || o.lx < 1 || o.nb < 4 || o.ty * kb > 256 || (o.ty * kb) % 32) return;
+  if (sweep_smem_bytes(nz, elem, o) > 220 * 1024 || (uint64_t)3 * (o.ty + 2) * nz * elem >= (1u << 20)) return;
+  c = o;
+}
+
 void select_kernels(advect_ctx& ctx) {
-  ctx.fwd_kind = 0;
+  const Member& m = ctx.members[0];
+  ctx.sweep = default_sweep(m.nz, elem_of((int)ctx.dtype));
+  sweep_override(ctx.sweep, m.nz, elem_of((int)ctx.dtype));
+  ctx.fwd_kind = ctx.sweep.ty > 0 ? 1 : 0;
+  ctx.fwd_name = ctx.fwd_kind ? "fwd_sweep" : "fwd_point";
   ctx.adj_kind = 0;
-  ctx.fwd_name = "fwd_point";
   ctx.adj_name = "adj_point";
 }
 
 cudaError_t launch_fwd(const advect_ctx& ctx, const FwdArgs& a, cudaStream_t st) {
+  if (ctx.fwd_kind == 1 && aligned16(a.u) && aligned16(a.v) && aligned16(a.w) && aligned16(a.su) &&
+      aligned16(a.sv) && aligned16(a.sw))
+    return launch_fwd_sweep((int)ctx.dtype, a, ctx.sweep, ctx.d_flag, st);
   return launch_fwd_point((int)ctx.dtype, a, st);
 }
 

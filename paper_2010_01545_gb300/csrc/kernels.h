@@ -29,13 +29,19 @@ struct AdjArgs {
 
 // Plane-sweep tile configuration (see fwd_sweep.cu).
 struct SweepCfg {
-  int ty;       // rows (y) per CTA
-  int lx;       // x-planes per CTA
-  int threads;  // threads per CTA
+  int ty;  // rows (y) per CTA
+  int lx;  // x-planes per CTA
+  int nb;  // shared-memory plane slots (>= 4)
 };
 
 // One thread per grid point, plain loads: any shape and alignment.
 cudaError_t launch_fwd_point(int dtype, const FwdArgs& a, cudaStream_t st);
 cudaError_t launch_adj_point(int dtype, const AdjArgs& a, cudaStream_t st);
+
+// Plane sweep: needs nz % sweep_vec(elem) == 0, nz * elem % 16 == 0, 16-byte
+// aligned fields, ty * nz / sweep_vec(elem) a multiple of 32 and <= 256.
+int sweep_vec(int elem);
+size_t sweep_smem_bytes(int nz, int elem, const SweepCfg& cfg);
+cudaError_t launch_fwd_sweep(int dtype, const FwdArgs& a, const SweepCfg& cfg, int* flag, cudaStream_t st);
 
 }  // namespace advect

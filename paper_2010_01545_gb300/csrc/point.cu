@@ -71,7 +71,7 @@ fwd_point_kernel(FwdArgs a) {
            tcy * (vym * (v0 + vym) - vyp * (v0 + vyp));
       ow = tcx * (wxm * (uxm + uxm_zp) - wxp * (u0 + uzp)) +
            tcy * (wym * (vym + vym_zp) - wyp * (v0 + vzp));
-      if (sizeof(C) == 4 && k <= a.f64_levels) {
+      if (sizeof(C) == 4 && a.f64_levels > 0 && k <= a.f64_levels) {
         // near-surface levels: vertical terms in binary64 with binary64 tables
         const double* d = a.c.d;
         const double c1 = d[k], c2 = d[nz + k], d1 = d[2 * nz + k], d2 = d[3 * nz + k];

@@ -46,6 +46,7 @@ def _check_sample(outs, winds, grid, shape, tol, seed):
 def test_forward_f64_2048x2048x64_sampled(big_winds):
     shape = (2048, 2048, 64)
     op, grid = make_op(shape, "f64")
+    assert op.kernel_name() == "fwd_sweep"
     outs = op.forward(*(dev(a) for a in big_winds))
     torch.cuda.synchronize()
     _check_sample(outs, big_winds, grid, shape, 1e-12, 1)
