@@ -20,7 +20,7 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 // Default plane-sweep tile for a column height and element size; ty = 0 when
 // the sweep kernel cannot take this shape.
 SweepCfg default_sweep(int nz, int elem) {
-  SweepCfg c{0, 64, 4};
+  SweepCfg c{0, 64, 4, 1};
   const int P = sweep_vec(elem);
   if (nz % P || (nz * elem) % 16) return c;
   const int kb = nz / P;
@@ -36,9 +36,14 @@ SweepCfg default_sweep(int nz, int elem) {
     if ((ty * kb) % 32) return c;
   }
   c.ty = ty;
-  // a deep ring keeps enough bytes in flight to cover HBM latency
-  c.nb = elem == 2 ? 16 : 8;
-  while (c.nb > 4 && sweep_smem_bytes(nz, elem, c) > 72 * 1024) --c.nb;
+  // FP32/F16S: registers capped for four 128-thread CTAs per SM (no spills),
+  // which beat three or one larger CTA on the 2048 x 2048 x 64 grid; the ring
+  // then gets a quarter of the SM's shared memory.  FP64 is bound by the FP64
+  // pipe and keeps the uncapped allocation.
+  c.occ = (elem <= 4 && ty * kb <= 128) ? 4 : 1;
+  const size_t cap = c.occ == 4 ? 54 * 1024 : 72 * 1024;
+  c.nb = elem == 2 ? 12 : (elem == 4 ? 6 : 7);
+  while (c.nb > 4 && sweep_smem_bytes(nz, elem, c) > cap) --c.nb;
   while (c.ty > 1 && sweep_smem_bytes(nz, elem, c) > 220 * 1024) {
     int t = c.ty - 1;
     while (t > 1 && (t * kb) % 32) --t;
@@ -50,14 +55,18 @@ SweepCfg default_sweep(int nz, int elem) {
   return c;
 }
 
-// ADVECT_SWEEP="ty,lx,nb" overrides the plane-sweep tile (ignored unless valid).
+// ADVECT_SWEEP="ty,lx,nb[,occ]" overrides the plane-sweep tile (ignored unless valid).
 static void sweep_override(SweepCfg& c, int nz, int elem) {
   const char* s = getenv("ADVECT_SWEEP");
   if (!s || c.ty == 0) return;
-  SweepCfg o{0, 0, 0};
-  if (sscanf(s, "%d,%d,%d", &o.ty, &o.lx, &o.nb) != 3) return;
+  SweepCfg o{0, 0, 0, 1};
+  const int n = sscanf(s, "%d,%d,%d,%d", &o.ty, &o.lx, &o.nb, &o.occ);
+  if (n < 3) return;
+  if (n == 3) o.occ = 1;
   const int kb = nz / sweep_vec(elem);
   if (o.ty < 1 || o.lx < 1 || o.nb < 4 || o.ty * kb > 256 || (o.ty * kb) % 32) return;
+  if (o.occ != 1 && o.occ != 3 && o.occ != 4) return;
+  if (o.occ != 1 && o.ty * kb > 128) return;
   if (sweep_smem_bytes(nz, elem, o) > 220 * 1024 || (uint64_t)3 * (o.ty + 2) * nz * elem >= (1u << 20)) return;
   c = o;
 }

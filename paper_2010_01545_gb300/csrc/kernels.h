@@ -29,9 +29,10 @@ struct AdjArgs {
 
 // Plane-sweep tile configuration (see fwd_sweep.cu).
 struct SweepCfg {
-  int ty;  // rows (y) per CTA
-  int lx;  // x-planes per CTA
-  int nb;  // shared-memory plane slots (>= 4)
+  int ty;   // rows (y) per CTA
+  int lx;   // x-planes per CTA
+  int nb;   // shared-memory plane slots (>= 4)
+  int occ;  // CTAs per SM the register allocation is capped for (1, 3 or 4)
 };
 
 // One thread per grid point, plain loads: any shape and alignment.

@@ -1,0 +1,413 @@
+// sweep_core.cuh -- the plane-sweep machinery shared by the single-grid and
+// ensemble forward kernels.
+//
+// A tile is TY rows (j0 .. j0+TY-1) of one grid over the x-planes
+// [i_lo, i_hi).  For each plane the CTA needs the (TY+2)-row slab
+// j0-1 .. j0+TY of u, v and w, which in the [nx][ny][nz] layout is one
+// contiguous run per field (three runs where the periodic wrap in y splits
+// it).  The slabs stream through a ring of NB shared-memory slots filled by
+// cp.async.bulk (the TMA engine) with one mbarrier per slot counting the
+// bytes.  There is no CTA-wide barrier per plane: each warp, when done with a
+// slot, bumps that slot's arrival counter, and the last warp to arrive issues
+// the copy of the plane NB ahead into it.  So warps drift within the ring and
+// overlap each other's latencies.
+//
+// Thread (row rr, k-block kb) owns P consecutive levels of one column for the
+// whole tile.  The own-row values of planes i-1 and i, the off-row values
+// reused one plane later, and the face sums shared between consecutive
+// planes stay in registers; vertical neighbours come from the adjacent lanes
+// by shuffle.  Each plane then costs nine vector loads from shared memory per
+// thread.  Per point the arithmetic and its order follow Listing 1 (Sec. 2.1)
+// for su and the same pattern for sv and sw; the lid branch comes from
+// tzc2[nz-1] == 0 and zero values above the top level.
+#pragma once
+
+#include "bulk.cuh"
+#include "kernels.h"
+
+namespace advect {
+namespace sweep {
+
+template <typename T>
+struct VecIO;
+
+template <>
+struct VecIO<double> {
+  static constexpr int P = 2;
+  using C = double;
+  __device__ static __forceinline__ void ld(const double* s, float, C (&o)[P]) {
+    const double2 x = *reinterpret_cast<const double2*>(s);
+    o[0] = x.x;
+    o[1] = x.y;
+  }
+  __device__ static __forceinline__ C ld1(const double* s, float) { return *s; }
+  __device__ static __forceinline__ void st(double* g, const C (&v)[P], float) {
+    __stcs(reinterpret_cast<double2*>(g), make_double2(v[0], v[1]));
+  }
+};
+
+template <>
+struct VecIO<float> {
+  static constexpr int P = 4;
+  using C = float;
+  __device__ static __forceinline__ void ld(const float* s, float, C (&o)[P]) {
+    const float4 x = *reinterpret_cast<const float4*>(s);
+    o[0] = x.x;
+    o[1] = x.y;
+    o[2] = x.z;
+    o[3] = x.w;
+  }
+  __device__ static __forceinline__ C ld1(const float* s, float) { return *s; }
+  __device__ static __forceinline__ void st(float* g, const C (&v)[P], float) {
+    __stcs(reinterpret_cast<float4*>(g), make_float4(v[0], v[1], v[2], v[3]));
+  }
+};
+
+template <>
+struct VecIO<__half> {
+  static constexpr int P = 4;
+  using C = float;
+  __device__ static __forceinline__ void ld(const __half* s, float sc, C (&o)[P]) {
+    const uint2 x = *reinterpret_cast<const uint2*>(s);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&x.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&x.y));
+    o[0] = a.x * sc;
+    o[1] = a.y * sc;
+    o[2] = b.x * sc;
+    o[3] = b.y * sc;
+  }
+  __device__ static __forceinline__ C ld1(const __half* s, float sc) { return __half2float(*s) * sc; }
+  __device__ static __forceinline__ void st(__half* g, const C (&v)[P], float inv) {
+    const __half2 a = __floats2half2_rn(v[0] * inv, v[1] * inv);
+    const __half2 b = __floats2half2_rn(v[2] * inv, v[3] * inv);
+    uint2 x;
+    x.x = *reinterpret_cast<const uint32_t*>(&a);
+    x.y = *reinterpret_cast<const uint32_t*>(&b);
+    __stcs(reinterpret_cast<uint2*>(g), x);
+  }
+};
+
+// Shared-memory ring: NB slots of slot_cap bytes, then NB mbarriers, then NB
+// arrival counters and NB issue counters.
+struct Ring {
+  unsigned char* slots;
+  uint64_t* full;
+  int* arrived;  // warps done with the slot, cumulative over the tile
+  int* issued;   // copies issued into the slot during the tile
+  int nb;
+  size_t slot_cap;
+};
+
+__host__ __device__ inline size_t ring_bytes(int nb, size_t slot_cap) {
+  return (size_t)nb * slot_cap + (size_t)nb * sizeof(uint64_t) + 2 * (size_t)nb * sizeof(int);
+}
+
+__device__ inline Ring make_ring(unsigned char* smem, int nb, size_t slot_cap) {
+  Ring r;
+  r.slots = smem;
+  r.full = reinterpret_cast<uint64_t*>(smem + (size_t)nb * slot_cap);
+  r.arrived = reinterpret_cast<int*>(smem + (size_t)nb * slot_cap + (size_t)nb * sizeof(uint64_t));
+  r.issued = r.arrived + nb;
+  r.nb = nb;
+  r.slot_cap = slot_cap;
+  return r;
+}
+
+// One tile of one grid.
+template <typename T>
+struct Tile {
+  const T* f[3];  // u, v, w
+  T* o[3];        // su, sv, sw
+  int nx, ny, nz;
+  int j0, ty, kb;  // first row, rows per tile, k-blocks per row (nz / P)
+  int i_lo, i_hi;  // x-planes computed
+  Coeffs c;
+  Scales sc;
+  int f64_levels;
+};
+
+// Bulk-copy plane ql of the tile (x index i_lo-1+ql, periodic) into its slot.
+template <typename T>
+__device__ __forceinline__ void issue_plane(const Tile<T>& t, const Ring& R, int ql) {
+  const int slot = ql % R.nb;
+  int ig = t.i_lo - 1 + ql;
+  ig = ig < 0 ? ig + t.nx : (ig >= t.nx ? ig - t.nx : ig);
+  const int ty_eff = min(t.ty, t.ny - t.j0);
+  const int rows = t.ty + 2;
+  const uint32_t row_bytes = (uint32_t)(t.nz * sizeof(T));
+  uint64_t* bar = &R.full[slot];
+  R.issued[slot] += 1;  // one issuer per slot at a time
+  mbar_arrive_expect_tx(bar, 3u * (uint32_t)(ty_eff + 2) * row_bytes);
+  T* dst0 = reinterpret_cast<T*>(R.slots + (size_t)slot * R.slot_cap);
+  const int j0 = t.j0;
+  for (int f = 0; f < 3; ++f) {
+    const T* plane = t.f[f] + (size_t)ig * t.ny * t.nz;
+    T* dst = dst0 + (size_t)f * rows * t.nz;
+    if (j0 >= 1 && j0 + ty_eff <= t.ny - 1) {
+      bulk_copy_g2s(dst, plane + (size_t)(j0 - 1) * t.nz, (uint32_t)(ty_eff + 2) * row_bytes, bar);
+    } else {
+      const int jt = j0 == 0 ? t.ny - 1 : j0 - 1;
+      const int jb = j0 + ty_eff == t.ny ? 0 : j0 + ty_eff;
+      bulk_copy_g2s(dst, plane + (size_t)jt * t.nz, row_bytes, bar);
+      bulk_copy_g2s(dst + t.nz, plane + (size_t)j0 * t.nz, (uint32_t)ty_eff * row_bytes, bar);
+      bulk_copy_g2s(dst + (size_t)(ty_eff + 1) * t.nz, plane + (size_t)jb * t.nz, row_bytes, bar);
+    }
+  }
+}
+
+// Vertical halo of a P-vector: the values just below (k0-1) and just above
+// (k0+P) the thread's levels, taken from the neighbouring lanes of the same
+// row; zero beyond the column; a shared-memory read where the row crosses a
+// warp boundary (only when a row spans more than one warp).
+template <typename T, typename C, int P>
+__device__ __forceinline__ C halo_below(const C (&a)[P], const T* row, int k0, int kb, int lane, bool split,
+                                        float sc) {
+  C below = __shfl_up_sync(0xffffffffu, a[P - 1], 1);
+  if (split && lane == 0 && kb > 0) below = VecIO<T>::ld1(row + k0 - 1, sc);
+  return kb == 0 ? C(0) : below;
+}
+
+template <typename T, typename C, int P>
+__device__ __forceinline__ C halo_above(const C (&a)[P], const T* row, int k0, int kb, int KB, int lane,
+                                        bool split, float sc) {
+  C above = __shfl_down_sync(0xffffffffu, a[0], 1);
+  if (split && lane == 31 && kb < KB - 1) above = VecIO<T>::ld1(row + k0 + P, sc);
+  return kb == KB - 1 ? C(0) : above;
+}
+
+// Sweep one tile with the whole CTA.  The caller guarantees that the ring is
+// idle (no copy in flight, no thread reading it) on entry; on exit every copy
+// this call issued has completed or, after a timeout, been waited for with a
+// bounded budget.  Returns false if any wait of this thread's warp timed out.
+template <typename T>
+__device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
+  using IO = VecIO<T>;
+  using C = typename IO::C;
+  using S = Store<T>;
+  constexpr int P = IO::P;
+  const int NB = R.nb;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int KB = t.kb, nz = t.nz, ny = t.ny;
+  const int active_threads = t.ty * KB;  // a multiple of 32
+  const int nwarps = active_threads >> 5;
+  const int nplanes = t.i_hi - t.i_lo + 2;  // planes i_lo-1 .. i_hi
+  const int rows = t.ty + 2;
+
+  // Fresh barriers for this tile.
+  if (tid == 0) {
+    for (int s = 0; s < NB; ++s) {
+      mbar_init(&R.full[s], 1);
+      R.arrived[s] = 0;
+      R.issued[s] = 0;
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int q = 0; q < NB && q < nplanes; ++q) issue_plane(t, R, q);
+  }
+  bool ok = true;
+  if (tid < active_threads) {
+    const int kb = tid % KB, rr = tid / KB;
+    const int k0 = kb * P;
+    const int j = t.j0 + rr;
+    const bool row_ok = j < ny;
+    const bool split = (32 % KB) != 0;  // a row may straddle two warps
+    const float s_u = t.sc.in[0], s_v = t.sc.in[1], s_w = t.sc.in[2];
+    const int r = rr + 1;
+    const int o_u0 = r * nz, o_um = (r - 1) * nz, o_up = (r + 1) * nz;
+    const int o_v0 = (rows + r) * nz, o_vm = (rows + r - 1) * nz, o_vp = (rows + r + 1) * nz;
+    const int o_w0 = (2 * rows + r) * nz, o_wm = (2 * rows + r - 1) * nz, o_wp = (2 * rows + r + 1) * nz;
+    auto slot_ptr = [&](int ql) -> const T* {
+      return reinterpret_cast<const T*>(R.slots + (size_t)(ql % NB) * R.slot_cap);
+    };
+    int timed_out = 0;
+    auto wait_plane = [&](int ql) {
+      if (!mbar_wait_bounded(&R.full[ql % NB], (uint32_t)((ql / NB) & 1))) {
+        timed_out = 1;
+        atomicExch(flag, 1);
+      }
+    };
+    // Done with plane ql's slot: the last warp to arrive refills it.
+    auto release = [&](int ql) {
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence_block();
+        const int target = (ql / NB + 1) * nwarps;
+        const int prev = atomicAdd(&R.arrived[ql % NB], 1);
+        if (prev + 1 == target && ql + NB < nplanes) {
+          __threadfence_block();
+          fence_proxy_async_smem();
+          issue_plane(t, R, ql + NB);
+        }
+      }
+    };
+
+    C c1[P], c2[P], d1[P], d2[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int k = min(k0 + q, nz - 1);
+      c1[q] = S::coef(t.c, TZC1, nz, k);
+      c2[q] = S::coef(t.c, TZC2, nz, k);
+      d1[q] = S::coef(t.c, TZD1, nz, k);
+      d2[q] = S::coef(t.c, TZD2, nz, k);
+    }
+    const C tcx = S::tcx(t.c), tcy = S::tcy(t.c);
+
+    C UXM[P], U0[P], UXMYP[P], VXM[P], V0[P], VYM[P], WXM[P], W0[P];
+    C SXm[P], SVm[P], SWm[P];
+    C u0m, u0p, uxmp, v0m, v0p, vymp, w0m, w0p;
+    wait_plane(0);
+    wait_plane(1);
+    {
+      const T* P0 = slot_ptr(0);
+      const T* P1 = slot_ptr(1);
+      IO::ld(P0 + o_u0 + k0, s_u, UXM);
+      IO::ld(P1 + o_u0 + k0, s_u, U0);
+      IO::ld(P0 + o_up + k0, s_u, UXMYP);
+      IO::ld(P0 + o_v0 + k0, s_v, VXM);
+      IO::ld(P1 + o_v0 + k0, s_v, V0);
+      IO::ld(P1 + o_vm + k0, s_v, VYM);
+      IO::ld(P0 + o_w0 + k0, s_w, WXM);
+      IO::ld(P1 + o_w0 + k0, s_w, W0);
+      u0m = halo_below<T, C, P>(U0, P1 + o_u0, k0, kb, lane, split, s_u);
+      u0p = halo_above<T, C, P>(U0, P1 + o_u0, k0, kb, KB, lane, split, s_u);
+      uxmp = halo_above<T, C, P>(UXM, P0 + o_u0, k0, kb, KB, lane, split, s_u);
+      v0m = halo_below<T, C, P>(V0, P1 + o_v0, k0, kb, lane, split, s_v);
+      v0p = halo_above<T, C, P>(V0, P1 + o_v0, k0, kb, KB, lane, split, s_v);
+      vymp = halo_above<T, C, P>(VYM, P1 + o_vm, k0, kb, KB, lane, split, s_v);
+      w0m = halo_below<T, C, P>(W0, P1 + o_w0, k0, kb, lane, split, s_w);
+      w0p = halo_above<T, C, P>(W0, P1 + o_w0, k0, kb, KB, lane, split, s_w);
+    }
+    release(0);
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      SXm[q] = UXM[q] + U0[q];
+      SVm[q] = UXM[q] + UXMYP[q];
+      SWm[q] = UXM[q] + (q < P - 1 ? UXM[q + 1] : uxmp);
+    }
+    const bool f64z = sizeof(C) == 4 && t.f64_levels > 0 && k0 <= t.f64_levels;
+
+    for (int i = t.i_lo; i < t.i_hi; ++i) {
+      const int qn = i - t.i_lo + 2;  // plane i+1
+      const int qc = qn - 1;          // plane i
+      wait_plane(qn);
+      if (__any_sync(0xffffffffu, timed_out)) break;
+      const T* Pc = slot_ptr(qc);
+      const T* Pn = slot_ptr(qn);
+      C UXP[P], UYM[P], UYP[P], VXP[P], VYP[P], VXPYM[P], WXP[P], WYM[P], WYP[P];
+      IO::ld(Pn + o_u0 + k0, s_u, UXP);
+      IO::ld(Pc + o_um + k0, s_u, UYM);
+      IO::ld(Pc + o_up + k0, s_u, UYP);
+      IO::ld(Pn + o_v0 + k0, s_v, VXP);
+      IO::ld(Pc + o_vp + k0, s_v, VYP);
+      IO::ld(Pn + o_vm + k0, s_v, VXPYM);
+      IO::ld(Pn + o_w0 + k0, s_w, WXP);
+      IO::ld(Pc + o_wm + k0, s_w, WYM);
+      IO::ld(Pc + o_wp + k0, s_w, WYP);
+      const C uxpm = halo_below<T, C, P>(UXP, Pn + o_u0, k0, kb, lane, split, s_u);
+      const C uxpp = halo_above<T, C, P>(UXP, Pn + o_u0, k0, kb, KB, lane, split, s_u);
+      const C vxpm = halo_below<T, C, P>(VXP, Pn + o_v0, k0, kb, lane, split, s_v);
+      const C vxpp = halo_above<T, C, P>(VXP, Pn + o_v0, k0, kb, KB, lane, split, s_v);
+      const C wxpm = halo_below<T, C, P>(WXP, Pn + o_w0, k0, kb, lane, split, s_w);
+      const C wxpp = halo_above<T, C, P>(WXP, Pn + o_w0, k0, kb, KB, lane, split, s_w);
+      const C vxpymp = halo_above<T, C, P>(VXPYM, Pn + o_vm, k0, kb, KB, lane, split, s_v);
+      const C wypm = halo_below<T, C, P>(WYP, Pc + o_wp, k0, kb, lane, split, s_w);
+      // plane i is no longer read from shared memory by this warp
+      release(qc);
+
+      C ou[P], ov[P], ow[P];
+      C wu_lo = w0m + wxpm;   // w(i,k-1) + w(i+1,k-1): lower face of the u cell
+      C wv_lo = w0m + wypm;   // w(i,j,k-1) + w(i,j+1,k-1): lower face of the v cell
+      C ww_lo = W0[0] + w0m;  // w(k) + w(k-1): lower face of the w cell
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const C uzm = q > 0 ? U0[q - 1] : u0m;
+        const C uzp = q < P - 1 ? U0[q + 1] : u0p;
+        const C vzm = q > 0 ? V0[q - 1] : v0m;
+        const C vzp = q < P - 1 ? V0[q + 1] : v0p;
+        const C wzm = q > 0 ? W0[q - 1] : w0m;
+        const C wzp = q < P - 1 ? W0[q + 1] : w0p;
+        const C vym_zp = q < P - 1 ? VYM[q + 1] : vymp;
+        // su (Listing 1)
+        const C sx = U0[q] + UXP[q];
+        const C xu = UXM[q] * SXm[q] - UXP[q] * sx;
+        const C yu = UYM[q] * (VYM[q] + VXPYM[q]) - UYP[q] * (V0[q] + VXP[q]);
+        const C wu_hi = W0[q] + WXP[q];
+        // sv
+        const C sv_x = U0[q] + UYP[q];
+        const C xv = VXM[q] * SVm[q] - VXP[q] * sv_x;
+        const C yv = VYM[q] * (V0[q] + VYM[q]) - VYP[q] * (V0[q] + VYP[q]);
+        const C wv_hi = W0[q] + WYP[q];
+        // sw
+        const C sw_x = U0[q] + uzp;
+        const C xw = WXM[q] * SWm[q] - WXP[q] * sw_x;
+        const C yw = WYM[q] * (VYM[q] + vym_zp) - WYP[q] * (V0[q] + vzp);
+        const C ww_hi = W0[q] + wzp;
+        C hu = tcx * xu + tcy * yu;
+        C hv = tcx * xv + tcy * yv;
+        C hw = tcx * xw + tcy * yw;
+        const int k = k0 + q;
+        if (f64z && k >= 1 && k <= t.f64_levels) {
+          const double* dt = t.c.d;
+          const double e1 = dt[k], e2 = dt[nz + k], e3 = dt[2 * nz + k], e4 = dt[3 * nz + k];
+          hu = (C)((double)hu + e1 * (double)uzm * (double)wu_lo - e2 * (double)uzp * (double)wu_hi);
+          hv = (C)((double)hv + e1 * (double)vzm * (double)wv_lo - e2 * (double)vzp * (double)wv_hi);
+          hw = (C)((double)hw + e3 * (double)wzm * (double)ww_lo - e4 * (double)wzp * (double)ww_hi);
+        } else {
+          hu = hu + c1[q] * uzm * wu_lo - c2[q] * uzp * wu_hi;
+          hv = hv + c1[q] * vzm * wv_lo - c2[q] * vzp * wv_hi;
+          hw = hw + d1[q] * wzm * ww_lo - d2[q] * wzp * ww_hi;
+        }
+        ou[q] = k >= 1 ? hu : C(0);
+        ov[q] = k >= 1 ? hv : C(0);
+        ow[q] = (k >= 1 && k < nz - 1) ? hw : C(0);
+        SXm[q] = sx;
+        SVm[q] = sv_x;
+        SWm[q] = sw_x;
+        wu_lo = wu_hi;
+        wv_lo = wv_hi;
+        ww_lo = ww_hi;
+      }
+      if (row_ok) {
+        const size_t o = ((size_t)i * ny + j) * nz + k0;
+        IO::st(t.o[0] + o, ou, t.sc.inv_out[0]);
+        IO::st(t.o[1] + o, ov, t.sc.inv_out[1]);
+        IO::st(t.o[2] + o, ow, t.sc.inv_out[2]);
+      }
+      uxmp = u0p;
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        UXM[q] = U0[q];
+        U0[q] = UXP[q];
+        UXMYP[q] = UYP[q];
+        VXM[q] = V0[q];
+        V0[q] = VXP[q];
+        VYM[q] = VXPYM[q];
+        WXM[q] = W0[q];
+        W0[q] = WXP[q];
+      }
+      u0m = uxpm;
+      u0p = uxpp;
+      v0m = vxpm;
+      v0p = vxpp;
+      vymp = vxpymp;
+      w0m = wxpm;
+      w0p = wxpp;
+    }
+    ok = !timed_out;
+  }
+  // All warps are done with the tile; after a timeout, wait (bounded) for
+  // the last copy issued into each slot before the ring is reused or freed.
+  const int any_fail = __syncthreads_or(!ok);
+  if (any_fail && tid == 0) {
+    for (int s = 0; s < NB; ++s) {
+      const int n = R.issued[s];  // the copy of phase n-1 is the only one that can be pending
+      if (n > 0) mbar_wait_bounded(&R.full[s], (uint32_t)((n - 1) & 1), 1 << 20);
+    }
+  }
+  return !any_fail;
+}
+
+}  // namespace sweep
+}  // namespace advect
