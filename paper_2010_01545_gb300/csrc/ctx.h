@@ -43,7 +43,8 @@ struct advect_ctx {
   std::vector<advect::Member> members;
   std::string fwd_name, adj_name;
   int fwd_kind = 0, adj_kind = 0;  // kernel variant chosen at create time
-  advect::SweepCfg sweep{};
+  advect::SweepCfg sweep{};      // forward plane-sweep tile (ty == 0: not usable)
+  advect::SweepCfg adj_sweep{};  // adjoint plane-sweep tile
   advect::HostPath hp;
   void* ens = nullptr;  // ensemble state (ens.cu)
 

@@ -6,6 +6,7 @@
 #include <cstdlib>
 
 #include "ctx.h"
+#include "sweep_core.cuh"
 
 namespace advect {
 
@@ -55,30 +56,58 @@ SweepCfg default_sweep(int nz, int elem) {
   return c;
 }
 
-// ADVECT_SWEEP="ty,lx,nb[,occ]" overrides the plane-sweep tile (ignored unless valid).
-static void sweep_override(SweepCfg& c, int nz, int elem) {
-  const char* s = getenv("ADVECT_SWEEP");
+// A tile override "ty,lx,nb[,occ]" from the environment (ignored unless valid):
+// ADVECT_SWEEP for the forward, ADVECT_ADJ_SWEEP for the adjoint.
+static void sweep_override(const char* var, SweepCfg& c, int nz, int elem, int vec, int nf) {
+  const char* s = getenv(var);
   if (!s || c.ty == 0) return;
   SweepCfg o{0, 0, 0, 1};
   const int n = sscanf(s, "%d,%d,%d,%d", &o.ty, &o.lx, &o.nb, &o.occ);
   if (n < 3) return;
   if (n == 3) o.occ = 1;
-  const int kb = nz / sweep_vec(elem);
+  const int kb = nz / vec;
   if (o.ty < 1 || o.lx < 1 || o.nb < 4 || o.ty * kb > 256 || (o.ty * kb) % 32) return;
   if (o.occ != 1 && o.occ != 3 && o.occ != 4) return;
   if (o.occ != 1 && o.ty * kb > 128) return;
-  if (sweep_smem_bytes(nz, elem, o) > 220 * 1024 || (uint64_t)3 * (o.ty + 2) * nz * elem >= (1u << 20)) return;
+  const size_t smem = sweep::ring_bytes(o.nb, (size_t)nf * (o.ty + 2) * nz * elem);
+  if (smem > 220 * 1024 || (uint64_t)nf * (o.ty + 2) * nz * elem >= (1u << 20)) return;
   c = o;
+}
+
+// Default adjoint tile (six streamed fields): ~256 threads for binary64,
+// 128 for binary32; ty = 0 when the shape does not fit the sweep.
+SweepCfg default_adj_sweep(int nz, int elem) {
+  SweepCfg c{0, 64, 4, 1};
+  if (elem != 8 && elem != 4) return c;
+  const int P = adj_sweep_vec(elem);
+  if (nz % P || (nz * elem) % 16) return c;
+  const int kb = nz / P;
+  const int target = elem == 8 ? 256 : 128;
+  if (kb > target) return c;
+  int ty = target / kb;
+  while (ty > 1 && (ty * kb) % 32) --ty;
+  if ((ty * kb) % 32) return c;
+  c.ty = ty;
+  c.occ = (elem == 4 && ty * kb <= 128) ? 4 : 1;
+  const size_t cap = c.occ == 4 ? 54 * 1024 : 100 * 1024;
+  c.nb = 8;
+  while (c.nb > 4 && adj_sweep_smem_bytes(nz, elem, c) > cap) --c.nb;
+  if (adj_sweep_smem_bytes(nz, elem, c) > 220 * 1024 || (uint64_t)6 * (c.ty + 2) * nz * elem >= (1u << 20))
+    c.ty = 0;
+  return c;
 }
 
 void select_kernels(advect_ctx& ctx) {
   const Member& m = ctx.members[0];
   ctx.sweep = default_sweep(m.nz, elem_of((int)ctx.dtype));
-  sweep_override(ctx.sweep, m.nz, elem_of((int)ctx.dtype));
+  const int elem = elem_of((int)ctx.dtype);
+  sweep_override("ADVECT_SWEEP", ctx.sweep, m.nz, elem, sweep_vec(elem), 3);
   ctx.fwd_kind = ctx.sweep.ty > 0 ? 1 : 0;
   ctx.fwd_name = ctx.fwd_kind ? "fwd_sweep" : "fwd_point";
-  ctx.adj_kind = 0;
-  ctx.adj_name = "adj_point";
+  ctx.adj_sweep = default_adj_sweep(m.nz, elem);
+  sweep_override("ADVECT_ADJ_SWEEP", ctx.adj_sweep, m.nz, elem, adj_sweep_vec(elem), 6);
+  ctx.adj_kind = ctx.adj_sweep.ty > 0 ? 1 : 0;
+  ctx.adj_name = ctx.adj_kind ? "adj_sweep" : "adj_point";
 }
 
 cudaError_t launch_fwd(const advect_ctx& ctx, const FwdArgs& a, cudaStream_t st) {
@@ -89,6 +118,9 @@ cudaError_t launch_fwd(const advect_ctx& ctx, const FwdArgs& a, cudaStream_t st)
 }
 
 cudaError_t launch_adj(const advect_ctx& ctx, const AdjArgs& a, cudaStream_t st) {
+  if (ctx.adj_kind == 1 && aligned16(a.u) && aligned16(a.v) && aligned16(a.w) && aligned16(a.dsu) &&
+      aligned16(a.dsv) && aligned16(a.dsw) && aligned16(a.du) && aligned16(a.dv) && aligned16(a.dw))
+    return launch_adj_sweep((int)ctx.dtype, a, ctx.adj_sweep, ctx.d_flag, st);
   return launch_adj_point((int)ctx.dtype, a, st);
 }
 

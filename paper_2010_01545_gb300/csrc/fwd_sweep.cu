@@ -24,6 +24,7 @@ __global__ void __launch_bounds__(OCC == 1 ? 256 : 128, OCC) fwd_sweep_kernel(Sw
   t.f[0] = (const T*)p.a.u;
   t.f[1] = (const T*)p.a.v;
   t.f[2] = (const T*)p.a.w;
+  t.nf = 3;
   t.o[0] = (T*)p.a.su;
   t.o[1] = (T*)p.a.sv;
   t.o[2] = (T*)p.a.sw;

@@ -116,8 +116,9 @@ __device__ inline Ring make_ring(unsigned char* smem, int nb, size_t slot_cap) {
 // One tile of one grid.
 template <typename T>
 struct Tile {
-  const T* f[3];  // u, v, w
-  T* o[3];        // su, sv, sw
+  const T* f[6];  // inputs: u, v, w (forward); u, v, w, dsu, dsv, dsw (adjoint)
+  T* o[3];        // outputs: su, sv, sw or du, dv, dw
+  int nf;         // number of input fields streamed per plane
   int nx, ny, nz;
   int j0, ty, kb;  // first row, rows per tile, k-blocks per row (nz / P)
   int i_lo, i_hi;  // x-planes computed
@@ -126,8 +127,9 @@ struct Tile {
   int f64_levels;
 };
 
-// Bulk-copy plane ql of the tile (x index i_lo-1+ql, periodic) into its slot.
-template <typename T>
+// Bulk-copy plane ql of the tile (x index i_lo-1+ql, periodic) into its slot;
+// NF fields (t.nf == NF).
+template <int NF, typename T>
 __device__ __forceinline__ void issue_plane(const Tile<T>& t, const Ring& R, int ql) {
   const int slot = ql % R.nb;
   int ig = t.i_lo - 1 + ql;
@@ -137,10 +139,11 @@ __device__ __forceinline__ void issue_plane(const Tile<T>& t, const Ring& R, int
   const uint32_t row_bytes = (uint32_t)(t.nz * sizeof(T));
   uint64_t* bar = &R.full[slot];
   R.issued[slot] += 1;  // one issuer per slot at a time
-  mbar_arrive_expect_tx(bar, 3u * (uint32_t)(ty_eff + 2) * row_bytes);
+  mbar_arrive_expect_tx(bar, (uint32_t)NF * (uint32_t)(ty_eff + 2) * row_bytes);
   T* dst0 = reinterpret_cast<T*>(R.slots + (size_t)slot * R.slot_cap);
   const int j0 = t.j0;
-  for (int f = 0; f < 3; ++f) {
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
     const T* plane = t.f[f] + (size_t)ig * t.ny * t.nz;
     T* dst = dst0 + (size_t)f * rows * t.nz;
     if (j0 >= 1 && j0 + ty_eff <= t.ny - 1) {
@@ -151,6 +154,68 @@ __device__ __forceinline__ void issue_plane(const Tile<T>& t, const Ring& R, int
       bulk_copy_g2s(dst, plane + (size_t)jt * t.nz, row_bytes, bar);
       bulk_copy_g2s(dst + t.nz, plane + (size_t)j0 * t.nz, (uint32_t)ty_eff * row_bytes, bar);
       bulk_copy_g2s(dst + (size_t)(ty_eff + 1) * t.nz, plane + (size_t)jb * t.nz, row_bytes, bar);
+    }
+  }
+}
+
+// Fresh barriers and counters for a tile, then the first NB copies.  The
+// caller guarantees the ring is idle.
+template <int NF, typename T>
+__device__ __forceinline__ void start_tile(const Tile<T>& t, const Ring& R, int nplanes) {
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < R.nb; ++s) {
+      mbar_init(&R.full[s], 1);
+      R.arrived[s] = 0;
+      R.issued[s] = 0;
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int q = 0; q < R.nb && q < nplanes; ++q) issue_plane<NF>(t, R, q);
+  }
+}
+
+// End of a tile: all warps are done; after a timeout, wait (bounded) for the
+// last copy issued into each slot; then invalidate the barriers so the ring
+// can be re-initialised.  Returns true if no thread reported a timeout.
+__device__ __forceinline__ bool finish_tile(const Ring& R, bool ok) {
+  const int any_fail = __syncthreads_or(!ok);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < R.nb; ++s) {
+      const int n = R.issued[s];  // the copy of phase n-1 is the only one that can be pending
+      if (any_fail && n > 0) mbar_wait_bounded(&R.full[s], (uint32_t)((n - 1) & 1), 1 << 20);
+      mbar_inval(&R.full[s]);
+    }
+  }
+  __syncthreads();
+  return !any_fail;
+}
+
+// Wait for plane ql of the tile; false (and the error flag raised) if the
+// bounded wait ran out.
+__device__ __forceinline__ bool wait_plane(const Ring& R, int ql, int* flag) {
+  if (mbar_wait_bounded(&R.full[ql % R.nb], (uint32_t)((ql / R.nb) & 1))) return true;
+  atomicExch(flag, 1);
+  return false;
+}
+
+// This warp is done reading plane ql's slot; the last of the tile's nwarps
+// warps to arrive issues the copy of plane ql + NB into it.
+template <int NF, typename T>
+__device__ __forceinline__ void release_plane(const Tile<T>& t, const Ring& R, int ql, int nplanes, int nwarps,
+                                              int lane) {
+  __syncwarp();
+  if (lane == 0) {
+    __threadfence_block();
+    const int NB = R.nb;
+    const int target = (ql / NB + 1) * nwarps;
+    const int prev = atomicAdd(&R.arrived[ql % NB], 1);
+    if (prev + 1 == target && ql + NB < nplanes) {
+      __threadfence_block();
+      fence_proxy_async_smem();
+      issue_plane<NF>(t, R, ql + NB);
     }
   }
 }
@@ -193,19 +258,7 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
   const int nplanes = t.i_hi - t.i_lo + 2;  // planes i_lo-1 .. i_hi
   const int rows = t.ty + 2;
 
-  // Fresh barriers for this tile.
-  if (tid == 0) {
-    for (int s = 0; s < NB; ++s) {
-      mbar_init(&R.full[s], 1);
-      R.arrived[s] = 0;
-      R.issued[s] = 0;
-    }
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if (tid == 0) {
-    for (int q = 0; q < NB && q < nplanes; ++q) issue_plane(t, R, q);
-  }
+  start_tile<3>(t, R, nplanes);
   bool ok = true;
   if (tid < active_threads) {
     const int kb = tid % KB, rr = tid / KB;
@@ -222,26 +275,10 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
       return reinterpret_cast<const T*>(R.slots + (size_t)(ql % NB) * R.slot_cap);
     };
     int timed_out = 0;
-    auto wait_plane = [&](int ql) {
-      if (!mbar_wait_bounded(&R.full[ql % NB], (uint32_t)((ql / NB) & 1))) {
-        timed_out = 1;
-        atomicExch(flag, 1);
-      }
+    auto wait = [&](int ql) {
+      if (!wait_plane(R, ql, flag)) timed_out = 1;
     };
-    // Done with plane ql's slot: the last warp to arrive refills it.
-    auto release = [&](int ql) {
-      __syncwarp();
-      if (lane == 0) {
-        __threadfence_block();
-        const int target = (ql / NB + 1) * nwarps;
-        const int prev = atomicAdd(&R.arrived[ql % NB], 1);
-        if (prev + 1 == target && ql + NB < nplanes) {
-          __threadfence_block();
-          fence_proxy_async_smem();
-          issue_plane(t, R, ql + NB);
-        }
-      }
-    };
+    auto release = [&](int ql) { release_plane<3>(t, R, ql, nplanes, nwarps, lane); };
 
     C c1[P], c2[P], d1[P], d2[P];
 #pragma unroll
@@ -257,8 +294,8 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
     C UXM[P], U0[P], UXMYP[P], VXM[P], V0[P], VYM[P], WXM[P], W0[P];
     C SXm[P], SVm[P], SWm[P];
     C u0m, u0p, uxmp, v0m, v0p, vymp, w0m, w0p;
-    wait_plane(0);
-    wait_plane(1);
+    wait(0);
+    wait(1);
     {
       const T* P0 = slot_ptr(0);
       const T* P1 = slot_ptr(1);
@@ -291,7 +328,7 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
     for (int i = t.i_lo; i < t.i_hi; ++i) {
       const int qn = i - t.i_lo + 2;  // plane i+1
       const int qc = qn - 1;          // plane i
-      wait_plane(qn);
+      wait(qn);
       if (__any_sync(0xffffffffu, timed_out)) break;
       const T* Pc = slot_ptr(qc);
       const T* Pn = slot_ptr(qn);
@@ -397,16 +434,7 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
     }
     ok = !timed_out;
   }
-  // All warps are done with the tile; after a timeout, wait (bounded) for
-  // the last copy issued into each slot before the ring is reused or freed.
-  const int any_fail = __syncthreads_or(!ok);
-  if (any_fail && tid == 0) {
-    for (int s = 0; s < NB; ++s) {
-      const int n = R.issued[s];  // the copy of phase n-1 is the only one that can be pending
-      if (n > 0) mbar_wait_bounded(&R.full[s], (uint32_t)((n - 1) & 1), 1 << 20);
-    }
-  }
-  return !any_fail;
+  return finish_tile(R, ok);
 }
 
 }  // namespace sweep

@@ -55,3 +55,28 @@ def test_sweep_is_selected_for_aligned_columns():
     for shape, dtype in [((16, 16, 65), "f64"), ((16, 16, 6), "f32"), ((16, 16, 12), "f16s")]:
         op, _ = make_op(shape, dtype)
         assert op.kernel_name() == "fwd_point", (shape, dtype)
+
+
+ADJ_CASES = {"f64": [(4, 64, 8), (1, 5, 4), (2, 33, 6), (2, 1, 5, 3)],
+             "f32": [(4, 64, 6, 4), (1, 7, 4), (8, 300, 5), (2, 2, 6, 3)]}
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("shape", [(37, 45, 64), (3, 2, 64), (9, 70, 32)])
+def test_adjoint_sweep_configs_match_oracle(monkeypatch, dtype, shape):
+    from gpu_util import oracle_adjoint
+    x = workload.winds(*shape, seed=78)
+    lam = workload.cotangents(*shape, seed=79)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    if dtype == "f32":
+        x = [a.astype(np.float32).astype(np.float64) for a in x]
+        lam = [a.astype(np.float32).astype(np.float64) for a in lam]
+    for cfg in ADJ_CASES[dtype]:
+        monkeypatch.setenv("ADVECT_ADJ_SWEEP", ",".join(map(str, cfg)))
+        op, grid = make_op(shape, dtype)
+        assert op.kernel_name(True) == "adj_sweep", cfg
+        got = op.adjoint(*(dev(a, tdt) for a in (*x, *lam)))
+        ref = oracle_adjoint(*x, *lam, grid)
+        for g, r in zip(got, ref):
+            assert normwise(host(g), r) <= (1e-12 if dtype == "f64" else 5e-6), cfg
+        op.close()
