@@ -184,6 +184,23 @@ advect_status advect_ensemble_adjoint(advect_ctx *ctx, const void *const *u, con
                                       void *const *du, void *const *dv, void *const *dw,
                                       advect_stream stream);
 
+/*
+ * Autotuning (ensembles: tile length in x, ring depth and register cap;
+ * single grids: the same plus the point kernel).  enable != 0: the next
+ * forward and the next adjoint call on this context time every candidate on
+ * that call's own buffers (CUDA events on the call's stream; the call
+ * synchronises with its stream), keep the fastest, write it to the tuning
+ * cache ($ADVECT_TUNE_CACHE, else ~/.cache/advect_gb300/tune.json) and finish
+ * with it, so the outputs are those of the chosen kernel.  Contexts created
+ * later for the same shapes, type and SM count start from the cached choice.
+ * ADVECT_TUNE=1 in the environment enables this for every new context.  The
+ * tiling never changes the arithmetic of a point.
+ */
+advect_status advect_autotune(advect_ctx *ctx, int enable);
+
+/* The tile configuration in use for forward (0) or adjoint (1), as text. */
+const char *advect_tuned_config(const advect_ctx *ctx, int adjoint);
+
 /* Wait for the context's work on `stream` and report any device-side timeout. */
 advect_status advect_sync(advect_ctx *ctx, advect_stream stream);
 

@@ -45,6 +45,7 @@ EXPORTS = (
     "advect_forward_host", "advect_f16s_output_scales", "advect_set_f64_levels",
     "advect_ensemble_create", "advect_ensemble_forward", "advect_ensemble_adjoint",
     "advect_sync", "advect_kernel_name", "advect_destroy", "advect_last_error",
+    "advect_autotune", "advect_tuned_config",
 )
 
 _lib = None
@@ -93,6 +94,10 @@ def lib():
     L.advect_sync.restype = st
     L.advect_kernel_name.argtypes = [_vp, ctypes.c_int]
     L.advect_kernel_name.restype = ctypes.c_char_p
+    L.advect_autotune.argtypes = [_vp, ctypes.c_int]
+    L.advect_autotune.restype = st
+    L.advect_tuned_config.argtypes = [_vp, ctypes.c_int]
+    L.advect_tuned_config.restype = ctypes.c_char_p
     L.advect_destroy.argtypes = [_vp]
     L.advect_destroy.restype = None
     L.advect_last_error.argtypes = []
@@ -207,6 +212,14 @@ def advect_sync(ctx, stream=0) -> None:
 
 def advect_kernel_name(ctx, adjoint=False) -> str:
     return lib().advect_kernel_name(ctx, 1 if adjoint else 0).decode()
+
+
+def advect_autotune(ctx, enable=True) -> None:
+    _check(lib().advect_autotune(ctx, 1 if enable else 0))
+
+
+def advect_tuned_config(ctx, adjoint=False) -> str:
+    return lib().advect_tuned_config(ctx, 1 if adjoint else 0).decode()
 
 
 def advect_destroy(ctx) -> None:

@@ -16,12 +16,15 @@
 #include <vector>
 
 #include "../../include/advect.h"
+#include "abi_util.h"
 #include "ctx.h"
 #include "kernels.h"
 
 using namespace advect;
+using namespace advect::abi;
 
-namespace {
+namespace advect {
+namespace abi {
 
 thread_local std::string g_last_error;
 
@@ -169,6 +172,11 @@ Coeffs coeffs_of(const Member& m) {
   return c;
 }
 
+}  // namespace abi
+}  // namespace advect
+
+namespace {
+
 advect_status read_scales(advect_ctx* ctx, const float* scales, Scales& sc) {
   for (int q = 0; q < 3; ++q) {
     sc.in[q] = 1.f;
@@ -202,6 +210,11 @@ advect_status advect_ctx::launch_forward(const void* u, const void* v, const voi
   a.f64_levels = f64_levels;
   a.i0 = i0;
   a.i1 = i1;
+  if (tune_fwd) {
+    tune_fwd = false;
+    cudaError_t e = tune_single(*this, 0, &a, nullptr, st);
+    if (e != cudaSuccess) return cuda_fail(e, "forward tuning");
+  }
   cudaError_t e = launch_fwd(*this, a, st);
   if (e != cudaSuccess) return cuda_fail(e, "forward kernel launch");
   return ADVECT_OK;
@@ -315,6 +328,11 @@ advect_status advect_adjoint(advect_ctx* ctx, const void* u, const void* v, cons
   a.du = du; a.dv = dv; a.dw = dw;
   a.s = Shape{m.nx, m.ny, m.nz};
   a.c = coeffs_of(m);
+  if (ctx->tune_adj) {
+    ctx->tune_adj = false;
+    cudaError_t e = tune_single(*ctx, 1, nullptr, &a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint tuning");
+  }
   cudaError_t e = launch_adj(*ctx, a, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel launch");
   return ADVECT_OK;

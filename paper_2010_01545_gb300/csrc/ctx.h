@@ -47,6 +47,8 @@ struct advect_ctx {
   advect::SweepCfg adj_sweep{};  // adjoint plane-sweep tile
   advect::HostPath hp;
   void* ens = nullptr;  // ensemble state (ens.cu)
+  bool tune_fwd = false, tune_adj = false;  // tune on the next forward / adjoint call
+  std::string cfg_text[2];                  // storage for advect_tuned_config
 
   advect_status launch_forward(const void* u, const void* v, const void* w, void* su, void* sv,
                                void* sw, const advect::Scales& sc, int i0, int i1, cudaStream_t st);
@@ -57,6 +59,7 @@ struct advect_ctx {
 namespace advect {
 // Kernel selection and launch (dispatch.cu).
 void select_kernels(advect_ctx& ctx);
+cudaError_t tune_single(advect_ctx& ctx, int adj, const FwdArgs* fa, const AdjArgs* aa, cudaStream_t st);
 cudaError_t launch_fwd(const advect_ctx& ctx, const FwdArgs& a, cudaStream_t st);
 cudaError_t launch_adj(const advect_ctx& ctx, const AdjArgs& a, cudaStream_t st);
 }  // namespace advect

@@ -6,7 +6,13 @@
 #include <cstdlib>
 
 #include "ctx.h"
+#include "ens.h"
 #include "sweep_core.cuh"
+#include "tune.h"
+
+#include <functional>
+#include <string>
+#include <vector>
 
 namespace advect {
 
@@ -97,6 +103,130 @@ SweepCfg default_adj_sweep(int nz, int elem) {
   return c;
 }
 
+namespace {
+
+const char* dname(int d) { return d == kF64 ? "f64" : (d == kF32 ? "f32" : "f16s"); }
+
+std::string single_key(const advect_ctx& ctx, int adj) {
+  const Member& m = ctx.members[0];
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  char buf[128];
+  snprintf(buf, sizeof buf, "%s|%s|%dx%dx%d|sm%d", adj ? "adj" : "fwd", dname((int)ctx.dtype), m.nx, m.ny, m.nz,
+           sms);
+  return buf;
+}
+
+std::string fmt_cfg(int kind, const SweepCfg& c) {
+  if (kind == 0) return "point";
+  char buf[64];
+  snprintf(buf, sizeof buf, "%d,%d,%d,%d", c.ty, c.lx, c.nb, c.occ);
+  return buf;
+}
+
+// Parse a cached choice; validates against the shape like the env override.
+bool parse_cfg(const std::string& v, int nz, int elem, int vec, int nf, int& kind, SweepCfg& c) {
+  if (v == "point") {
+    kind = 0;
+    return true;
+  }
+  SweepCfg o{0, 0, 0, 1};
+  if (sscanf(v.c_str(), "%d,%d,%d,%d", &o.ty, &o.lx, &o.nb, &o.occ) != 4) return false;
+  if (nz % vec || (nz * elem) % 16) return false;
+  const int kb = nz / vec;
+  if (o.ty < 1 || o.lx < 1 || o.nb < 4 || o.ty * kb > 256 || (o.ty * kb) % 32) return false;
+  if (o.occ != 1 && o.occ != 3 && o.occ != 4) return false;
+  if (o.occ != 1 && o.ty * kb > 128) return false;
+  if (sweep::ring_bytes(o.nb, (size_t)nf * (o.ty + 2) * nz * elem) > 220 * 1024) return false;
+  kind = 1;
+  c = o;
+  return true;
+}
+
+// Candidate tiles for a column height: 128-thread tiles with register caps
+// for 4 or 3 CTAs per SM and up-to-256-thread tiles without cap, over x-range
+// lengths and ring depths that fit the shared memory of those CTAs.
+std::vector<SweepCfg> candidates(int nz, int elem, int vec, int nf) {
+  std::vector<SweepCfg> out;
+  if (nz % vec || (nz * elem) % 16) return out;
+  const int kb = nz / vec;
+  for (int occ : {4, 3, 1}) {
+    const int threads = occ == 1 ? 256 : 128;
+    if (kb > threads) continue;
+    int ty = threads / kb;
+    while (ty > 1 && (ty * kb) % 32) --ty;
+    if ((ty * kb) % 32) continue;
+    for (int lx : {32, 64, 128})
+      for (int nb : {4, 6, 8, 12}) {
+        SweepCfg c{ty, lx, nb, occ};
+        const size_t smem = sweep::ring_bytes(nb, (size_t)nf * (ty + 2) * nz * elem);
+        if (smem > 220 * 1024 || smem * (occ == 1 ? 1 : occ) > 225 * 1024) continue;
+        if ((uint64_t)nf * (ty + 2) * nz * elem >= (1u << 20)) continue;
+        out.push_back(c);
+      }
+  }
+  return out;
+}
+
+float time_ms(cudaStream_t st, const std::function<cudaError_t()>& fn, cudaError_t& err) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  err = fn();
+  cudaEventRecord(a, st);
+  const int reps = 2;
+  for (int r = 0; r < reps && err == cudaSuccess; ++r) err = fn();
+  cudaEventRecord(b, st);
+  cudaEventSynchronize(b);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms / reps;
+}
+
+}  // namespace
+
+// Time the point kernel and every candidate tile on the call's buffers, keep
+// the fastest (in the context and the tuning cache).  The caller then runs
+// the call with the chosen kernel.
+cudaError_t tune_single(advect_ctx& ctx, int adj, const FwdArgs* fa, const AdjArgs* aa, cudaStream_t st) {
+  const Member& m = ctx.members[0];
+  const int elem = elem_of((int)ctx.dtype);
+  const int vec = adj ? adj_sweep_vec(elem) : sweep_vec(elem);
+  const int nf = adj ? 6 : 3;
+  int& kind = adj ? ctx.adj_kind : ctx.fwd_kind;
+  SweepCfg& cfg = adj ? ctx.adj_sweep : ctx.sweep;
+  int best_kind = 0;
+  SweepCfg best = cfg;
+  cudaError_t e = cudaSuccess;
+  float best_ms = time_ms(st, [&]() {
+    return adj ? launch_adj_point((int)ctx.dtype, *aa, st) : launch_fwd_point((int)ctx.dtype, *fa, st);
+  }, e);
+  if (e != cudaSuccess) return e;
+  if (!(adj && ctx.dtype == ADVECT_F16S)) {
+    for (const SweepCfg& c : candidates(m.nz, elem, vec, nf)) {
+      const float ms = time_ms(st, [&]() {
+        return adj ? launch_adj_sweep((int)ctx.dtype, *aa, c, ctx.d_flag, st)
+                   : launch_fwd_sweep((int)ctx.dtype, *fa, c, ctx.d_flag, st);
+      }, e);
+      if (e != cudaSuccess) return e;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+        best_kind = 1;
+      }
+    }
+  }
+  kind = best_kind;
+  if (best_kind) cfg = best;
+  const std::string name = adj ? (kind ? "adj_sweep" : "adj_point") : (kind ? "fwd_sweep" : "fwd_point");
+  (adj ? ctx.adj_name : ctx.fwd_name) = name;
+  tune_cache_put(single_key(ctx, adj), fmt_cfg(kind, cfg));
+  return cudaSuccess;
+}
+
 void select_kernels(advect_ctx& ctx) {
   const Member& m = ctx.members[0];
   ctx.sweep = default_sweep(m.nz, elem_of((int)ctx.dtype));
@@ -107,7 +237,23 @@ void select_kernels(advect_ctx& ctx) {
   ctx.adj_sweep = default_adj_sweep(m.nz, elem);
   sweep_override("ADVECT_ADJ_SWEEP", ctx.adj_sweep, m.nz, elem, adj_sweep_vec(elem), 6);
   ctx.adj_kind = ctx.adj_sweep.ty > 0 ? 1 : 0;
+  // a tuned choice from the cache wins over the defaults; an environment
+  // override wins over both
+  for (int adj = 0; adj < 2; ++adj) {
+    std::string v;
+    const char* env = getenv(adj ? "ADVECT_ADJ_SWEEP" : "ADVECT_SWEEP");
+    if (env || !tune_cache_get(single_key(ctx, adj), v)) continue;
+    int kind = 0;
+    SweepCfg c{0, 0, 0, 1};
+    if (adj && ctx.dtype == ADVECT_F16S) continue;
+    if (parse_cfg(v, m.nz, elem, adj ? adj_sweep_vec(elem) : sweep_vec(elem), adj ? 6 : 3, kind, c)) {
+      (adj ? ctx.adj_kind : ctx.fwd_kind) = kind;
+      if (kind) (adj ? ctx.adj_sweep : ctx.sweep) = c;
+    }
+  }
+  ctx.fwd_name = ctx.fwd_kind ? "fwd_sweep" : "fwd_point";
   ctx.adj_name = ctx.adj_kind ? "adj_sweep" : "adj_point";
+  ctx.tune_fwd = ctx.tune_adj = tune_env_enabled();
 }
 
 cudaError_t launch_fwd(const advect_ctx& ctx, const FwdArgs& a, cudaStream_t st) {
@@ -158,6 +304,8 @@ advect_status advect_ctx::ensure_host_path(size_t bytes) {
 void advect_ctx::release() {
   using namespace advect;
   cudaDeviceSynchronize();
+  if (ens) ens_free(static_cast<EnsState*>(ens));
+  ens = nullptr;
   for (auto& m : members)
     if (m.d_tabs) cudaFree(m.d_tabs);
   members.clear();

@@ -58,6 +58,12 @@ class Advect:
     def kernel_name(self, adjoint=False):
         return _abi.advect_kernel_name(self.handle, adjoint)
 
+    def autotune(self, enable=True):
+        _abi.advect_autotune(self.handle, enable)
+
+    def tuned_config(self, adjoint=False):
+        return _abi.advect_tuned_config(self.handle, adjoint)
+
     def output_scales(self, in_scales):
         return _abi.advect_f16s_output_scales(self.handle, in_scales)
 
@@ -171,6 +177,12 @@ class AdvectEnsemble:
 
     def kernel_name(self, adjoint=False):
         return _abi.advect_kernel_name(self.handle, adjoint)
+
+    def autotune(self, enable=True):
+        _abi.advect_autotune(self.handle, enable)
+
+    def tuned_config(self, adjoint=False):
+        return _abi.advect_tuned_config(self.handle, adjoint)
 
     def sync(self):
         _abi.advect_sync(self.handle, _stream())

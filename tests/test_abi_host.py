@@ -123,3 +123,23 @@ def test_last_error_is_per_thread(lib):
     t.join()
     assert seen == [""]
     assert "invalid shape" in _abi.advect_last_error()
+
+
+def test_ensemble_create_validates_on_the_host(lib):
+    c8 = _coeffs(8)
+    with pytest.raises(_abi.AdvectError) as e:
+        _abi.advect_ensemble_create([], [], _abi.ADVECT_F32)
+    assert e.value.status == 1
+    with pytest.raises(_abi.AdvectError) as e:
+        _abi.advect_ensemble_create([(8, 8, 8)], [c8], _abi.ADVECT_F16S)
+    assert e.value.status == 4
+    c6 = _coeffs(6)
+    with pytest.raises(_abi.AdvectError) as e:   # nz * 4 bytes not a multiple of 16
+        _abi.advect_ensemble_create([(8, 8, 8), (8, 8, 6)], [c8, c6], _abi.ADVECT_F32)
+    assert e.value.status == 4 and "member 1" in str(e.value)
+    with pytest.raises(_abi.AdvectError) as e:
+        _abi.advect_ensemble_create([(8, 0, 8)], [c8], _abi.ADVECT_F32)
+    assert e.value.status == 1 and "member 0" in str(e.value)
+    assert lib.advect_ensemble_forward(None, *([None] * 6), None) == 1
+    assert lib.advect_autotune(None, 1) == 1
+    assert lib.advect_tuned_config(None, 0) == b""
