@@ -201,6 +201,43 @@ advect_status advect_autotune(advect_ctx *ctx, int enable);
 /* The tile configuration in use for forward (0) or adjoint (1), as text. */
 const char *advect_tuned_config(const advect_ctx *ctx, int adjoint);
 
+/*
+ * Forward pass that allocates no device memory (the paper has no counterpart;
+ * this exists for callers, not for the method).  Some callers may not call
+ * cudaMalloc: code inside a framework whose memory pool owns every device
+ * allocation, latency-critical loops where an allocation can block or
+ * synchronise the device, or programs that must keep their device footprint
+ * fixed after start-up.  advect_create allocates (tables, error flag); this
+ * call needs no context.
+ *
+ * Arguments are those of advect_create plus advect_forward: shape, host
+ * coefficient tables, element type, device fields (u, v, w in; su, sv, sw
+ * out; owned by the caller), F16S scales, stream.  Results equal
+ * advect_forward's for the same inputs (the same kernels run).
+ *
+ * Scratch: the coefficient tables and the kernels' error flag live in one
+ * fixed library array in device memory (ADVECT_NOALLOC_MAX_NZ levels,
+ * about 24 KB), which every GPU that loads the library holds until the
+ * process exits.  Each call rewrites the tables and clears the flag on its
+ * stream before the forward kernel runs.  All calls on a device share that
+ * one array: calls whose work can overlap on the GPU (different streams, or
+ * several host threads) race -- order them on one stream or serialise them.
+ * A kernel-side timeout (a bounded wait giving up, not expected in normal
+ * operation) is cleared by the next call without being reported; use the
+ * context API where those reports matter.
+ *
+ * The first call made on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture on that device.
+ *
+ * EINVAL if nz > ADVECT_NOALLOC_MAX_NZ, or for the argument errors of
+ * advect_create / advect_forward.
+ */
+#define ADVECT_NOALLOC_MAX_NZ 512
+advect_status advect_forward_noalloc(int nx, int ny, int nz, const advect_coeffs *c, advect_dtype dtype,
+                                     const void *u, const void *v, const void *w, void *su, void *sv,
+                                     void *sw, const float *scales, advect_stream stream);
+
 /* Wait for the context's work on `stream` and report any device-side timeout. */
 advect_status advect_sync(advect_ctx *ctx, advect_stream stream);
 

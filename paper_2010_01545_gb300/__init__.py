@@ -10,7 +10,8 @@ from ._abi import (ADVECT_F16S, ADVECT_F32, ADVECT_F64, AdvectError, advect_adjo
                    advect_ensemble_adjoint, advect_ensemble_create, advect_ensemble_forward,
                    advect_f16s_output_scales, advect_forward, advect_forward_host,
                    advect_kernel_name, advect_last_error, advect_set_f64_levels, advect_sync,
-                   advect_autotune, advect_tuned_config, library_path)
+                   advect_autotune, advect_tuned_config, advect_forward_noalloc,
+                   library_path)
 
 
 def __getattr__(name):

@@ -45,8 +45,10 @@ EXPORTS = (
     "advect_forward_host", "advect_f16s_output_scales", "advect_set_f64_levels",
     "advect_ensemble_create", "advect_ensemble_forward", "advect_ensemble_adjoint",
     "advect_sync", "advect_kernel_name", "advect_destroy", "advect_last_error",
-    "advect_autotune", "advect_tuned_config",
+    "advect_autotune", "advect_tuned_config", "advect_forward_noalloc",
 )
+
+NOALLOC_MAX_NZ = 512  # ADVECT_NOALLOC_MAX_NZ
 
 _lib = None
 
@@ -98,6 +100,9 @@ def lib():
     L.advect_autotune.restype = st
     L.advect_tuned_config.argtypes = [_vp, ctypes.c_int]
     L.advect_tuned_config.restype = ctypes.c_char_p
+    L.advect_forward_noalloc.argtypes = ([ctypes.c_int] * 3 + [ctypes.POINTER(advect_coeffs), ctypes.c_int]
+                                         + [_vp] * 6 + [ctypes.POINTER(ctypes.c_float), _vp])
+    L.advect_forward_noalloc.restype = st
     L.advect_destroy.argtypes = [_vp]
     L.advect_destroy.restype = None
     L.advect_last_error.argtypes = []
@@ -220,6 +225,15 @@ def advect_autotune(ctx, enable=True) -> None:
 
 def advect_tuned_config(ctx, adjoint=False) -> str:
     return lib().advect_tuned_config(ctx, 1 if adjoint else 0).decode()
+
+
+def advect_forward_noalloc(nx, ny, nz, coeffs, dtype, u, v, w, su, sv, sw, scales=None,
+                           stream=0) -> None:
+    """Context-free forward that allocates no device memory (see include/advect.h)."""
+    c, keep = _coeffs_struct(*coeffs)
+    _check(lib().advect_forward_noalloc(int(nx), int(ny), int(nz), ctypes.byref(c), int(dtype),
+                                        u, v, w, su, sv, sw, _scales(scales), stream))
+    del keep
 
 
 def advect_destroy(ctx) -> None:

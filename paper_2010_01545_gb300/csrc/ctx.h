@@ -59,6 +59,7 @@ struct advect_ctx {
 namespace advect {
 // Kernel selection and launch (dispatch.cu).
 void select_kernels(advect_ctx& ctx);
+SweepCfg default_sweep(int nz, int elem);  // ty == 0: the shape cannot use the plane sweep
 cudaError_t tune_single(advect_ctx& ctx, int adj, const FwdArgs* fa, const AdjArgs* aa, cudaStream_t st);
 cudaError_t launch_fwd(const advect_ctx& ctx, const FwdArgs& a, cudaStream_t st);
 cudaError_t launch_adj(const advect_ctx& ctx, const AdjArgs& a, cudaStream_t st);
