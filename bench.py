@@ -120,7 +120,7 @@ class ClockSampler:
 def profile_traffic(kernel_name, src_hash):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
     the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"{kernel_name}_2048x2048x64.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel_name}_f64_2048x2048x64.md")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -227,11 +227,18 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-variants", action="store_true", help="headline only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--shape", default=None,
+                    help="nx,ny,nz of a smaller forward case (profiling); not a bench line")
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "f16s"],
+                    help="element type of the --shape case")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.shape:
+        return run_case(args)
 
     import torch
     rank, world, local = dist_env()
@@ -279,24 +286,15 @@ def main():
     traffic = profile_traffic(fwd_name, src_hash)
     roofline = {"bound": "alu", "achieved": achieved_gflops, "peak": fp64_peak_gflops,
                 "unit": "GFLOP/s", "frac": achieved_gflops / fp64_peak_gflops, "traffic": traffic,
-                "kernel": fwd_name, "peak_kind": "FP64 pipe: 2 DFMA/clk/SM x 152 SM x max SM clock",
+                "kernel": fwd_name, "tile": op.tuned_config(),
+                "peak_kind": "FP64 pipe: 2 DFMA/clk/SM x 152 SM x max SM clock",
                 "hbm": {"achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s",
                         "frac": achieved_gbs / hbm_gbs, "peak_kind": peak_kind}}
 
     # end to end through the host-buffer C-ABI call (pinned host memory)
-    h_in = [torch.from_numpy(a).pin_memory() for a in winds]
-    h_out = [torch.empty(SHAPE, dtype=torch.float64).pin_memory() for _ in range(3)]
-    e2e_steps = max(3, min(args.steps, 10))
-    for _ in range(2):
-        op.forward_host(*h_in, h_out)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        op.forward_host(*h_in, h_out)
-    e2e_secs = (time.perf_counter() - t0) / e2e_steps
-    e2e = {"value": world * n_pts / e2e_secs, "unit": UNIT,
-           "h2d_bytes_per_step": 3 * n_pts * 8, "d2h_bytes_per_step": 3 * n_pts * 8,
-           "ms_per_step": 1e3 * e2e_secs}
-    del h_in, h_out
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, torch, op, winds, world, n_pts)
 
     ref_out = [t.clone() for t in d_out]
     variants = {}
@@ -330,6 +328,54 @@ def main():
     return 0
 
 
+def run_e2e(args, torch, op, winds, world, n_pts):
+    """Forward through advect_forward_host: pinned host buffers in and out, the
+    library's chunked copy/kernel pipeline inside the timed region."""
+    h_in = [torch.from_numpy(a).pin_memory() for a in winds]
+    h_out = [torch.empty(SHAPE, dtype=torch.float64).pin_memory() for _ in range(3)]
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        op.forward_host(*h_in, h_out)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        op.forward_host(*h_in, h_out)
+    e2e_secs = (time.perf_counter() - t0) / e2e_steps
+    return {"value": world * n_pts / e2e_secs, "unit": UNIT,
+            "h2d_bytes_per_step": 3 * n_pts * 8, "d2h_bytes_per_step": 3 * n_pts * 8,
+            "ms_per_step": 1e3 * e2e_secs}
+
+
+def run_case(args):
+    """A forward-only case of another shape / type, for profiling."""
+    import torch
+
+    import workload
+    from paper_2010_01545_gb300 import build, torch_api
+    build.build()
+    shape = tuple(int(x) for x in args.shape.split(","))
+    n_pts = shape[0] * shape[1] * shape[2]
+    grid = workload.vertical_grid(shape[2])
+    op = torch_api.Advect(*shape, torch_api.coefficients_from_grid(grid), args.dtype)
+    winds = workload.winds(*shape)
+    scales = None
+    if args.dtype == "f16s":
+        s_in = [float(2.0 ** np.ceil(np.log2(np.max(np.abs(a))))) for a in winds]
+        scales = s_in + op.output_scales(s_in)
+        d = [(torch.from_numpy(a).cuda() / s).to(torch.float16) for a, s in zip(winds, s_in)]
+    else:
+        d = [torch.from_numpy(a).to("cuda", op.torch_dtype) for a in winds]
+    out = [op.empty() for _ in range(3)]
+    for _ in range(args.warmup):
+        op.forward(*d, out=out, scales=scales)
+    secs = time_calls(lambda: op.forward(*d, out=out, scales=scales), args.steps,
+                      torch.cuda.current_stream()) / args.steps
+    print(json.dumps({"case": f"fwd_{args.dtype}_{shape[0]}x{shape[1]}x{shape[2]}",
+                      "kernel": op.kernel_name(), "tile": op.tuned_config(), "ms": 1e3 * secs,
+                      "points_per_s": n_pts / secs, "steps": args.steps, "warmup": args.warmup}),
+          flush=True)
+    return 0
+
+
 def run_variants(args, torch, torch_api, workload, winds, coeffs, ref_out, stream, hbm_gbs, grid):
     out = {}
     n_pts = SHAPE[0] * SHAPE[1] * SHAPE[2]
@@ -343,6 +389,7 @@ def run_variants(args, torch, torch_api, workload, winds, coeffs, ref_out, strea
     secs = time_calls(lambda: op32.forward(*d32, out=o32), steps, stream) / steps
     errs = normwise_errors(o32, ref_out)
     out["f32"] = {"value": n_pts / secs, "unit": UNIT, "ms": 1e3 * secs, "kernel": op32.kernel_name(),
+                  "tile": op32.tuned_config(),
                   "hbm_frac": BYTES_PER_POINT["f32"] * n_pts / secs / 1e9 / hbm_gbs,
                   "error_vs_f64": dict(zip(("su", "sv", "sw"), errs))}
     del d32, o32, op32
@@ -358,29 +405,68 @@ def run_variants(args, torch, torch_api, workload, winds, coeffs, ref_out, strea
     secs = time_calls(lambda: op16.forward(*d16, out=o16, scales=sc), steps, stream) / steps
     errs = normwise_errors([o.to(torch.float64) * s for o, s in zip(o16, s_out)], ref_out)
     out["f16s"] = {"value": n_pts / secs, "unit": UNIT, "ms": 1e3 * secs, "kernel": op16.kernel_name(),
+                   "tile": op16.tuned_config(),
                    "hbm_frac": BYTES_PER_POINT["f16s"] * n_pts / secs / 1e9 / hbm_gbs,
                    "error_vs_f64": dict(zip(("su", "sv", "sw"), errs)),
                    "note": "error includes the fp16 quantisation of the inputs"}
     del d16, o16, op16
     torch.cuda.empty_cache()
-    # adjoint on the 1024 x 1024 x 128 differentiation grid
+    # adjoint on the 1024 x 1024 x 128 differentiation grid (inputs drawn on
+    # the device: U(-10, 10) winds and N(0, 1) cotangents from a seeded
+    # torch generator)
     agrid = workload.vertical_grid(ADJ_SHAPE[2])
     acoef = torch_api.coefficients_from_grid(agrid)
     an = ADJ_SHAPE[0] * ADJ_SHAPE[1] * ADJ_SHAPE[2]
+    gen = torch.Generator(device="cuda")
     for name, tdt in (("f64", torch.float64), ("f32", torch.float32)):
+        gen.manual_seed(workload.DEFAULT_SEED)
         opa = torch_api.Advect(*ADJ_SHAPE, acoef, name)
-        x = [torch.from_numpy(a).to("cuda", tdt) for a in workload.winds(*ADJ_SHAPE, seed=7)]
-        lam = [torch.from_numpy(a).to("cuda", tdt) for a in workload.cotangents(*ADJ_SHAPE, seed=8)]
+        x = [torch.rand(ADJ_SHAPE, generator=gen, device="cuda", dtype=tdt) * 20 - 10 for _ in range(3)]
+        lam = [torch.randn(ADJ_SHAPE, generator=gen, device="cuda", dtype=tdt) for _ in range(3)]
         g = [opa.empty() for _ in range(3)]
         for _ in range(args.warmup):
             opa.adjoint(*x, *lam, out=g)
         secs = time_calls(lambda: opa.adjoint(*x, *lam, out=g), steps, stream) / steps
         out[f"adjoint_{name}_1024x1024x128"] = {
             "value": an / secs, "unit": UNIT, "ms": 1e3 * secs, "kernel": opa.kernel_name(True),
+            "tile": opa.tuned_config(True),
             "hbm_frac": ADJ_BYTES_PER_POINT[name] * an / secs / 1e9 / hbm_gbs}
         del x, lam, g, opa
         torch.cuda.empty_cache()
+    out["ensemble_f32_48"] = run_ensemble(args, torch, torch_api, workload, stream, hbm_gbs)
     return out
+
+
+def run_ensemble(args, torch, torch_api, workload, stream, hbm_gbs):
+    """48 members of uneven shape, FP32, forward and adjoint, autotuned tiles."""
+    shapes = workload.ensemble_shapes(48)
+    pts = sum(a * b * c for a, b, c in shapes)
+    coeffs = [torch_api.coefficients_from_grid(workload.vertical_grid(s[2])) for s in shapes]
+    ens = torch_api.AdvectEnsemble(shapes, coeffs, "f32")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(workload.DEFAULT_SEED)
+    x = [[torch.rand(s, generator=gen, device="cuda") * 20 - 10 for s in shapes] for _ in range(3)]
+    lam = [[torch.randn(s, generator=gen, device="cuda") for s in shapes] for _ in range(3)]
+    y = [ens.empty() for _ in range(3)]
+    g = [ens.empty() for _ in range(3)]
+    ens.autotune(True)
+    ens.forward(*x, out=y)          # tunes on these buffers, then runs the winner
+    ens.adjoint(*x, *lam, out=g)
+    steps = max(3, min(args.steps, 10))
+    res = {"members": len(shapes), "points": pts}
+    for name, fn, bpp in (("forward", lambda: ens.forward(*x, out=y), 24),
+                          ("adjoint", lambda: ens.adjoint(*x, *lam, out=g), 36)):
+        for _ in range(args.warmup):
+            fn()
+        secs = time_calls(fn, steps, stream) / steps
+        res[name] = {"value": pts / secs, "unit": UNIT, "ms": 1e3 * secs,
+                     "hbm_frac": bpp * pts / secs / 1e9 / hbm_gbs,
+                     "tile": ens.tuned_config(name == "adjoint"),
+                     "launch": "one persistent kernel, CUDA graph replay"}
+    del x, lam, y, g
+    ens.close()
+    torch.cuda.empty_cache()
+    return res
 
 
 if __name__ == "__main__":
