@@ -96,7 +96,7 @@ __device__ bool adjoint_tile(const Tile<T>& t, const Ring& R, int* flag) {
     };
     int timed_out = 0;
     auto wait = [&](int ql) {
-      if (!wait_plane(R, ql, flag)) timed_out = 1;
+      if (!wait_plane(R, ql, flag, t.wait_budget)) timed_out = 1;
     };
     auto release = [&](int ql) { release_plane<6>(t, R, ql, nplanes, nwarps, lane); };
     // cotangent masks: lu, lv live on k >= 1; lw on 1 <= k <= nz-2

@@ -40,6 +40,8 @@ __global__ void __launch_bounds__(OCC == 1 ? 256 : 128, OCC) adj_sweep_kernel(Ad
     t.sc.inv_out[q] = 1.f;
   }
   t.f64_levels = 0;
+  t.wait_budget = p.a.wait_budget;
+  t.skip_plane = p.a.skip_plane;
   sweep::adjoint_tile<T>(t, R, p.flag);
 }
 

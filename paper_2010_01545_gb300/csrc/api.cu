@@ -210,6 +210,8 @@ advect_status advect_ctx::launch_forward(const void* u, const void* v, const voi
   a.f64_levels = f64_levels;
   a.i0 = i0;
   a.i1 = i1;
+  a.wait_budget = wait_budget;
+  a.skip_plane = test_skip_plane;
   if (tune_fwd) {
     tune_fwd = false;
     cudaError_t e = tune_single(*this, 0, &a, nullptr, st);
@@ -328,6 +330,8 @@ advect_status advect_adjoint(advect_ctx* ctx, const void* u, const void* v, cons
   a.du = du; a.dv = dv; a.dw = dw;
   a.s = Shape{m.nx, m.ny, m.nz};
   a.c = coeffs_of(m);
+  a.wait_budget = ctx->wait_budget;
+  a.skip_plane = ctx->test_skip_plane;
   if (ctx->tune_adj) {
     ctx->tune_adj = false;
     cudaError_t e = tune_single(*ctx, 1, nullptr, &a, (cudaStream_t)stream);

@@ -48,6 +48,11 @@ struct advect_ctx {
   advect::HostPath hp;
   void* ens = nullptr;  // ensemble state (ens.cu)
   bool tune_fwd = false, tune_adj = false;  // tune on the next forward / adjoint call
+  // Test-only fault injection for the bounded-wait path (ADVECT_TEST_SKIP_PLANE,
+  // ADVECT_TEST_WAIT_CYCLES read at create time): the sweep kernels never issue
+  // the copy of that plane index of each tile, so waits on it run out.
+  int test_skip_plane = -1;
+  long long wait_budget = 2LL * 1000 * 1000 * 1000;
   std::string cfg_text[2];                  // storage for advect_tuned_config
 
   advect_status launch_forward(const void* u, const void* v, const void* w, void* su, void* sv,

@@ -254,6 +254,11 @@ void select_kernels(advect_ctx& ctx) {
   ctx.fwd_name = ctx.fwd_kind ? "fwd_sweep" : "fwd_point";
   ctx.adj_name = ctx.adj_kind ? "adj_sweep" : "adj_point";
   ctx.tune_fwd = ctx.tune_adj = tune_env_enabled();
+  if (const char* q = getenv("ADVECT_TEST_SKIP_PLANE")) ctx.test_skip_plane = atoi(q);
+  if (const char* b = getenv("ADVECT_TEST_WAIT_CYCLES")) {
+    const long long v = atoll(b);
+    if (v > 0) ctx.wait_budget = v;
+  }
 }
 
 cudaError_t launch_fwd(const advect_ctx& ctx, const FwdArgs& a, cudaStream_t st) {

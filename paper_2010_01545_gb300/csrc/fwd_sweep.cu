@@ -39,6 +39,8 @@ __global__ void __launch_bounds__(OCC == 1 ? 256 : 128, OCC) fwd_sweep_kernel(Sw
   t.c = p.a.c;
   t.sc = p.a.sc;
   t.f64_levels = p.a.f64_levels;
+  t.wait_budget = p.a.wait_budget;
+  t.skip_plane = p.a.skip_plane;
   sweep::forward_tile<T>(t, R, p.flag);
 }
 

@@ -18,6 +18,8 @@ struct FwdArgs {
   Scales sc;
   int f64_levels;  // F32/F16S: levels 1..f64_levels use binary64 vertical terms
   int i0, i1;      // x-planes [i0, i1) are computed (the others are untouched)
+  long long wait_budget = 2LL * 1000 * 1000 * 1000;  // clock64 cycles per bounded wait
+  int skip_plane = -1;  // test-only: plane index of each tile whose copy is never issued
 };
 
 struct AdjArgs {
@@ -25,6 +27,8 @@ struct AdjArgs {
   void *du, *dv, *dw;
   Shape s;
   Coeffs c;
+  long long wait_budget = 2LL * 1000 * 1000 * 1000;
+  int skip_plane = -1;
 };
 
 // Plane-sweep tile configuration (see fwd_sweep.cu).

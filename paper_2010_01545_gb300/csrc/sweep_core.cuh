@@ -125,6 +125,8 @@ struct Tile {
   Coeffs c;
   Scales sc;
   int f64_levels;
+  long long wait_budget = kWaitBudgetCycles;  // clock64 cycles per bounded wait
+  int skip_plane = -1;  // test-only fault injection: this plane's copy is never issued
 };
 
 // Bulk-copy plane ql of the tile (x index i_lo-1+ql, periodic) into its slot;
@@ -137,6 +139,7 @@ __device__ __forceinline__ void issue_plane(const Tile<T>& t, const Ring& R, int
   const int ty_eff = min(t.ty, t.ny - t.j0);
   const int rows = t.ty + 2;
   const uint32_t row_bytes = (uint32_t)(t.nz * sizeof(T));
+  if (ql == t.skip_plane) return;  // injected fault: waits on this plane must run out
   uint64_t* bar = &R.full[slot];
   R.issued[slot] += 1;  // one issuer per slot at a time
   mbar_arrive_expect_tx(bar, (uint32_t)NF * (uint32_t)(ty_eff + 2) * row_bytes);
@@ -185,8 +188,11 @@ __device__ __forceinline__ bool finish_tile(const Ring& R, bool ok) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < R.nb; ++s) {
       const int n = R.issued[s];  // the copy of phase n-1 is the only one that can be pending
-      if (any_fail && n > 0) mbar_wait_bounded(&R.full[s], (uint32_t)((n - 1) & 1), 1 << 20);
-      mbar_inval(&R.full[s]);
+      if (any_fail) {
+        if (n > 0) mbar_wait_bounded(&R.full[s], (uint32_t)((n - 1) & 1), 1 << 20);
+      } else {
+        mbar_inval(&R.full[s]);  // the ring is re-initialised for the next tile
+      }
     }
   }
   __syncthreads();
@@ -195,8 +201,8 @@ __device__ __forceinline__ bool finish_tile(const Ring& R, bool ok) {
 
 // Wait for plane ql of the tile; false (and the error flag raised) if the
 // bounded wait ran out.
-__device__ __forceinline__ bool wait_plane(const Ring& R, int ql, int* flag) {
-  if (mbar_wait_bounded(&R.full[ql % R.nb], (uint32_t)((ql / R.nb) & 1))) return true;
+__device__ __forceinline__ bool wait_plane(const Ring& R, int ql, int* flag, long long budget) {
+  if (mbar_wait_bounded(&R.full[ql % R.nb], (uint32_t)((ql / R.nb) & 1), budget)) return true;
   atomicExch(flag, 1);
   return false;
 }
@@ -276,7 +282,7 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
     };
     int timed_out = 0;
     auto wait = [&](int ql) {
-      if (!wait_plane(R, ql, flag)) timed_out = 1;
+      if (!wait_plane(R, ql, flag, t.wait_budget)) timed_out = 1;
     };
     auto release = [&](int ql) { release_plane<3>(t, R, ql, nplanes, nwarps, lane); };
 
