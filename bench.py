@@ -230,7 +230,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     ap.add_argument("--shape", default=None,
                     help="nx,ny,nz of a smaller forward case (profiling); not a bench line")
-    ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "f16s"],
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "f16s", "f64ff"],
                     help="element type of the --shape case")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -393,6 +393,20 @@ def run_variants(args, torch, torch_api, workload, winds, coeffs, ref_out, strea
                   "hbm_frac": BYTES_PER_POINT["f32"] * n_pts / secs / 1e9 / hbm_gbs,
                   "error_vs_f64": dict(zip(("su", "sv", "sw"), errs))}
     del d32, o32, op32
+    # binary64 storage, double-float arithmetic on the binary32 pipes
+    opff = torch_api.Advect(*SHAPE, coeffs, "f64ff")
+    dff = [torch.from_numpy(a).cuda() for a in winds]
+    off = [opff.empty() for _ in range(3)]
+    for _ in range(args.warmup):
+        opff.forward(*dff, out=off)
+    secs = time_calls(lambda: opff.forward(*dff, out=off), steps, stream) / steps
+    errs = normwise_errors(off, ref_out)
+    out["f64ff"] = {"value": n_pts / secs, "unit": UNIT, "ms": 1e3 * secs, "kernel": opff.kernel_name(),
+                    "tile": opff.tuned_config(),
+                    "hbm_frac": BYTES_PER_POINT["f64"] * n_pts / secs / 1e9 / hbm_gbs,
+                    "error_vs_f64": dict(zip(("su", "sv", "sw"), errs)),
+                    "note": "binary64 in memory, pairs of binary32 in arithmetic"}
+    del dff, off, opff
     # FP16 storage with per-field power-of-two scales
     op16 = torch_api.Advect(*SHAPE, coeffs, "f16s")
     s_in = [float(2.0 ** np.ceil(np.log2(np.max(np.abs(a))))) for a in winds]

@@ -5,7 +5,7 @@
 only in the CUDA library ``_build/libadvect.so`` (built by ``build.build``);
 a missing library is an error, never a fallback.
 """
-from ._abi import (ADVECT_F16S, ADVECT_F32, ADVECT_F64, AdvectError, advect_adjoint,  # noqa: F401
+from ._abi import (ADVECT_F16S, ADVECT_F32, ADVECT_F64, ADVECT_F64_FF, AdvectError, advect_adjoint,  # noqa: F401
                    advect_coeffs_from_grid, advect_create, advect_destroy,
                    advect_ensemble_adjoint, advect_ensemble_create, advect_ensemble_forward,
                    advect_f16s_output_scales, advect_forward, advect_forward_host,

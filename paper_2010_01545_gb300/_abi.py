@@ -14,7 +14,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libadvect.so")
 
-ADVECT_F64, ADVECT_F32, ADVECT_F16S = 0, 1, 2
+ADVECT_F64, ADVECT_F32, ADVECT_F16S, ADVECT_F64_FF = 0, 1, 2, 3
 STATUS_NAMES = {0: "ADVECT_OK", 1: "ADVECT_EINVAL", 2: "ADVECT_ENOMEM", 3: "ADVECT_ECUDA",
                 4: "ADVECT_EUNSUPPORTED", 5: "ADVECT_ETIMEOUT"}
 

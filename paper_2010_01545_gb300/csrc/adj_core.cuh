@@ -62,6 +62,16 @@ struct AdjIO<float> {
   }
 };
 
+template <>
+struct AdjIO<f64ff> {
+  static constexpr int P = 1;
+  using C = ff;
+  __device__ static __forceinline__ void ld(const f64ff* s, C (&o)[P]) { o[0] = ff(s->v); }
+  __device__ static __forceinline__ void st(f64ff* g, const C (&v)[P]) {
+    __stcs(reinterpret_cast<double*>(g), (double)v[0]);
+  }
+};
+
 template <typename T>
 __device__ bool adjoint_tile(const Tile<T>& t, const Ring& R, int* flag) {
   using IO = AdjIO<T>;

@@ -91,6 +91,7 @@ cudaError_t launch_adj_sweep(int dtype, const AdjArgs& a, const SweepCfg& cfg, i
   switch (dtype) {
     case kF64: return launch_t<double>(a, cfg, flag, st);
     case kF32: return launch_t<float>(a, cfg, flag, st);
+    case kF64FF: return launch_t<f64ff>(a, cfg, flag, st);
     default: return cudaErrorInvalidValue;
   }
 }

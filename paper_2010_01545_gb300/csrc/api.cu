@@ -48,9 +48,9 @@ advect_status cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
-size_t elem_bytes(advect_dtype d) { return d == ADVECT_F64 ? 8 : (d == ADVECT_F32 ? 4 : 2); }
+size_t elem_bytes(advect_dtype d) { return (d == ADVECT_F64 || d == ADVECT_F64_FF) ? 8 : (d == ADVECT_F32 ? 4 : 2); }
 
-bool valid_dtype(int d) { return d == ADVECT_F64 || d == ADVECT_F32 || d == ADVECT_F16S; }
+bool valid_dtype(int d) { return d == ADVECT_F64 || d == ADVECT_F32 || d == ADVECT_F16S || d == ADVECT_F64_FF; }
 
 // Host copy of one member's tables with the entries no formula reads set to
 // zero, and tzc2[nz-1] = 0 (Listing 1 drops the upper flux at the top).

@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ff.cuh"
+
 namespace advect {
 
 // Per-level coefficient tables on the device, 4 tables of nz entries each in
@@ -79,6 +81,24 @@ struct Store<__half> {
   }
   __device__ static __forceinline__ C tcx(const Coeffs& c) { return c.tcx_f; }
   __device__ static __forceinline__ C tcy(const Coeffs& c) { return c.tcy_f; }
+};
+
+// binary64 storage, double-float arithmetic (ff.cuh)
+template <>
+struct Store<f64ff> {
+  using C = ff;
+  static constexpr int kBytes = 8;
+  __device__ static __forceinline__ C load(const f64ff* p, size_t i, float) {
+    return ff(__ldg(reinterpret_cast<const double*>(p) + i));
+  }
+  __device__ static __forceinline__ void store(f64ff* p, size_t i, C v, float) {
+    reinterpret_cast<double*>(p)[i] = (double)v;
+  }
+  __device__ static __forceinline__ C coef(const Coeffs& c, int table, int nz, int k) {
+    return ff(__ldg(c.d + (size_t)table * nz + k));
+  }
+  __device__ static __forceinline__ C tcx(const Coeffs& c) { return ff(c.tcx); }
+  __device__ static __forceinline__ C tcy(const Coeffs& c) { return ff(c.tcy); }
 };
 
 __device__ __forceinline__ int wrap_dec(int a, int n) { return a == 0 ? n - 1 : a - 1; }

@@ -18,7 +18,7 @@ namespace advect {
 
 namespace {
 
-int elem_of(int dtype) { return dtype == kF64 ? 8 : (dtype == kF32 ? 4 : 2); }
+int elem_of(int dtype) { return (dtype == kF64 || dtype == kF64FF) ? 8 : (dtype == kF32 ? 4 : 2); }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
@@ -105,7 +105,7 @@ SweepCfg default_adj_sweep(int nz, int elem) {
 
 namespace {
 
-const char* dname(int d) { return d == kF64 ? "f64" : (d == kF32 ? "f32" : "f16s"); }
+const char* dname(int d) { return d == kF64 ? "f64" : (d == kF32 ? "f32" : (d == kF64FF ? "f64ff" : "f16s")); }
 
 std::string single_key(const advect_ctx& ctx, int adj) {
   const Member& m = ctx.members[0];
@@ -231,6 +231,12 @@ void select_kernels(advect_ctx& ctx) {
   const Member& m = ctx.members[0];
   ctx.sweep = default_sweep(m.nz, elem_of((int)ctx.dtype));
   const int elem = elem_of((int)ctx.dtype);
+  if (ctx.dtype == ADVECT_F64_FF && ctx.sweep.ty > 0 && ctx.sweep.ty * (m.nz / sweep_vec(elem)) <= 128) {
+    // double-float arithmetic is bound by the binary32 issue rate: three CTAs
+    // per SM (<= 168 registers, no spills) keep more warps in flight
+    ctx.sweep.occ = 3;
+    while (ctx.sweep.nb > 4 && sweep_smem_bytes(m.nz, elem, ctx.sweep) > 72 * 1024) --ctx.sweep.nb;
+  }
   sweep_override("ADVECT_SWEEP", ctx.sweep, m.nz, elem, sweep_vec(elem), 3);
   ctx.fwd_kind = ctx.sweep.ty > 0 ? 1 : 0;
   ctx.fwd_name = ctx.fwd_kind ? "fwd_sweep" : "fwd_point";

@@ -34,7 +34,7 @@ int sm_count() {
   return sms;
 }
 
-const char* dtype_name(advect_dtype d) { return d == ADVECT_F64 ? "f64" : (d == ADVECT_F32 ? "f32" : "f16s"); }
+const char* dtype_name(advect_dtype d) { return d == ADVECT_F64 ? "f64" : (d == ADVECT_F32 ? "f32" : "other"); }
 
 std::string ens_key(const advect_ctx& ctx, int adj) {
   // FNV-1a over the member shapes
@@ -173,7 +173,7 @@ advect_status advect_ensemble_create(int n, const int* nx, const int* ny, const 
   *out = nullptr;
   if (n < 1 || !nx || !ny || !nz || !c) return fail(ADVECT_EINVAL, "need n >= 1 and non-NULL shape/coefficient arrays");
   if (!valid_dtype(dtype)) return fail(ADVECT_EINVAL, "unknown dtype %d", (int)dtype);
-  if (dtype == ADVECT_F16S) return fail(ADVECT_EUNSUPPORTED, "ensembles support F64 and F32");
+  if (dtype == ADVECT_F16S || dtype == ADVECT_F64_FF) return fail(ADVECT_EUNSUPPORTED, "ensembles support F64 and F32");
   for (int m = 0; m < n; ++m) {
     advect_status s = check_shape(nx[m], ny[m], nz[m]);
     if (s) return fail(s, "member %d: %s", m, g_last_error.c_str());

@@ -1,0 +1,119 @@
+// ff.cuh -- "double-float" arithmetic: a binary64 value carried as an
+// unevaluated sum hi + lo of two binary32 numbers, computed on the binary32
+// pipes (74x the binary64 rate on GB300).
+//
+// Algorithms: Knuth's TwoSum and FMA-based TwoProduct (error-free
+// transformations), Dekker's Fast2Sum for renormalisation.  Sums are TwoSum
+// of the high parts with the low parts added in binary32; products are the
+// exact product of the high parts plus the two cross terms.  Neither is
+// renormalised: the low part of every intermediate stays below about 2^-22
+// times the magnitude of the operands it came from (after cancellation the
+// high part may be much smaller than that), so each rounding error is about
+// 2^-47 of the operands' magnitudes, which is the scale the normwise error of
+// the stencil is measured on.  The result is renormalised once, when it is
+// assembled into a double.  For the PW stencil, whose terms are at most a few
+// times the largest source term, the normwise error against binary64 is
+// about 1e-14 (the tests bound it by 1e-12).
+//
+// Conversions never touch the binary64 pipe: splitting a double into (hi, lo)
+// and assembling (hi, lo) into the nearest-below double are integer bit
+// operations plus binary32 arithmetic.  Range: magnitudes in [2^-80, 2^126];
+// smaller inputs lose relative precision (the low part underflows), zero is
+// exact, and non-finite inputs are not supported.
+#pragma once
+
+#include <stdint.h>
+
+namespace advect {
+
+struct ff {
+  float hi, lo;
+  __device__ __forceinline__ ff() {}
+  __device__ __forceinline__ ff(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ ff(int z) : hi((float)z), lo(0.f) {}  // C(0)
+  __device__ __forceinline__ explicit ff(double x);
+  __device__ __forceinline__ explicit operator double() const;
+};
+
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return ff(s, b - (s - a));
+}
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return ff(s, (a - (s - bb)) + (b - bb));
+}
+
+__device__ __forceinline__ ff operator+(const ff& x, const ff& y) {
+  const ff s = two_sum(x.hi, y.hi);
+  return ff(s.hi, s.lo + (x.lo + y.lo));
+}
+
+__device__ __forceinline__ ff operator-(const ff& x) { return ff(-x.hi, -x.lo); }
+__device__ __forceinline__ ff operator-(const ff& x, const ff& y) { return x + (-y); }
+
+__device__ __forceinline__ ff operator*(const ff& x, const ff& y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return ff(p, e);
+}
+
+__device__ __forceinline__ ff& operator+=(ff& x, const ff& y) { return x = x + y; }
+__device__ __forceinline__ ff& operator-=(ff& x, const ff& y) { return x = x - y; }
+
+// double -> (hi, lo): hi is x with its significand truncated to 24 bits
+// (exact in binary32); lo holds the next 23 bits of the remainder.
+__device__ __forceinline__ ff::ff(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint32_t top = (uint32_t)(b >> 32), bot = (uint32_t)b;
+  const uint32_t sign = top & 0x80000000u;
+  const int e = (int)((top >> 20) & 0x7ff) - 1023;  // unbiased exponent
+  const uint32_t hib = sign | ((uint32_t)(e + 127) << 23) | ((top & 0xfffffu) << 3) | (bot >> 29);
+  // remainder: the low 29 significand bits, scaled 2^(e-52); keep the top 23
+  const uint32_t rem = (bot & 0x1fffffffu) >> 6;
+  const float r = __uint_as_float(0x4b000000u | rem) - 8388608.0f;  // exact integer rem
+  const int se = e - 46 + 127;                                    // 2^(e-46)
+  const float scale = __uint_as_float((uint32_t)max(se, 1) << 23);
+  const float l = __uint_as_float(__float_as_uint(r * scale) | sign);
+  const bool tiny = e < -126;  // zero or below the binary32 normal range
+  hi = tiny ? __uint_as_float(sign) : __uint_as_float(hib);
+  lo = (tiny || se < 1) ? 0.f : l;
+}
+
+// (hi, lo) -> double: renormalise, then add lo into hi's binary64 pattern as
+// an integer multiple of hi's binary64 ulp (truncated).
+__device__ __forceinline__ ff::operator double() const {
+  // |hi| >= |lo| is not guaranteed after unnormalised arithmetic: order them
+  const ff n = fabsf(hi) >= fabsf(lo) ? fast_two_sum(hi, lo) : fast_two_sum(lo, hi);
+  const uint32_t hb = __float_as_uint(n.hi), lb = __float_as_uint(n.lo);
+  const uint32_t eh = (hb >> 23) & 0xffu;
+  const uint32_t mh = hb & 0x7fffffu;
+  const uint64_t d = ((uint64_t)(hb & 0x80000000u) << 32) | ((uint64_t)(eh + 896u) << 52) | ((uint64_t)mh << 29);
+  const uint32_t el = (lb >> 23) & 0xffu;
+  const uint32_t ml = (lb & 0x7fffffu) | 0x800000u;
+  const int sh = (int)el - (int)eh + 29;  // lo = ml * 2^(el-127-23), ulp(d) = 2^(eh-127-52)
+  uint64_t L = sh >= 0 ? ((uint64_t)ml << min(sh, 31)) : (uint64_t)(ml >> min(-sh, 31));
+  L = el == 0 ? 0ull : L;  // lo zero (or below the binary32 normal range)
+  const bool opposite = ((hb ^ lb) & 0x80000000u) != 0;
+  L = (opposite && mh == 0) ? L << 1 : L;  // hi a power of two: the result lies in the binade below
+  const uint64_t r = opposite ? d - L : d + L;
+  return eh == 0 ? 0.0 : __longlong_as_double((long long)r);  // zero (binary32 subnormals as zero)
+}
+
+__device__ __forceinline__ ff shfl_up(const ff& v, int d) {
+  return ff(__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d));
+}
+__device__ __forceinline__ ff shfl_down(const ff& v, int d) {
+  return ff(__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d));
+}
+
+// Storage tag: binary64 in memory, double-float arithmetic.
+struct f64ff {
+  double v;
+};
+
+}  // namespace advect

@@ -93,6 +93,7 @@ cudaError_t launch_fwd_sweep(int dtype, const FwdArgs& a, const SweepCfg& cfg, i
     case kF64: return launch_t<double>(a, cfg, flag, st);
     case kF32: return launch_t<float>(a, cfg, flag, st);
     case kF16S: return launch_t<__half>(a, cfg, flag, st);
+    case kF64FF: return launch_t<f64ff>(a, cfg, flag, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -8,7 +8,7 @@
 namespace advect {
 
 // Element type codes (same values as advect_dtype).
-enum Dtype { kF64 = 0, kF32 = 1, kF16S = 2 };
+enum Dtype { kF64 = 0, kF32 = 1, kF16S = 2, kF64FF = 3 };
 
 struct FwdArgs {
   const void *u, *v, *w;

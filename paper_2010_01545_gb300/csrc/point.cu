@@ -203,6 +203,7 @@ cudaError_t launch_fwd_point(int dtype, const FwdArgs& a, cudaStream_t st) {
     case kF64: fwd_point_kernel<double><<<g, kThreads, 0, st>>>(a); break;
     case kF32: fwd_point_kernel<float><<<g, kThreads, 0, st>>>(a); break;
     case kF16S: fwd_point_kernel<__half><<<g, kThreads, 0, st>>>(a); break;
+    case kF64FF: fwd_point_kernel<f64ff><<<g, kThreads, 0, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -214,6 +215,7 @@ cudaError_t launch_adj_point(int dtype, const AdjArgs& a, cudaStream_t st) {
   switch (dtype) {
     case kF64: adj_point_kernel<double><<<g, kThreads, 0, st>>>(a); break;
     case kF32: adj_point_kernel<float><<<g, kThreads, 0, st>>>(a); break;
+    case kF64FF: adj_point_kernel<f64ff><<<g, kThreads, 0, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

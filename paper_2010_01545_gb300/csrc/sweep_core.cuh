@@ -87,6 +87,29 @@ struct VecIO<__half> {
   }
 };
 
+template <>
+struct VecIO<f64ff> {
+  static constexpr int P = 2;
+  using C = ff;
+  __device__ static __forceinline__ void ld(const f64ff* s, float, C (&o)[P]) {
+    const double2 x = *reinterpret_cast<const double2*>(s);
+    o[0] = ff(x.x);
+    o[1] = ff(x.y);
+  }
+  __device__ static __forceinline__ C ld1(const f64ff* s, float) { return ff(s->v); }
+  __device__ static __forceinline__ void st(f64ff* g, const C (&v)[P], float) {
+    __stcs(reinterpret_cast<double2*>(g), make_double2((double)v[0], (double)v[1]));
+  }
+};
+
+// Warp shuffles for every arithmetic type.
+__device__ __forceinline__ float shfl_up_c(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_up_c(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ ff shfl_up_c(const ff& v) { return shfl_up(v, 1); }
+__device__ __forceinline__ float shfl_down_c(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_down_c(double v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ ff shfl_down_c(const ff& v) { return shfl_down(v, 1); }
+
 // Shared-memory ring: NB slots of slot_cap bytes, then NB mbarriers, then NB
 // arrival counters and NB issue counters.
 struct Ring {
@@ -233,7 +256,7 @@ __device__ __forceinline__ void release_plane(const Tile<T>& t, const Ring& R, i
 template <typename T, typename C, int P>
 __device__ __forceinline__ C halo_below(const C (&a)[P], const T* row, int k0, int kb, int lane, bool split,
                                         float sc) {
-  C below = __shfl_up_sync(0xffffffffu, a[P - 1], 1);
+  C below = shfl_up_c(a[P - 1]);
   if (split && lane == 0 && kb > 0) below = VecIO<T>::ld1(row + k0 - 1, sc);
   return kb == 0 ? C(0) : below;
 }
@@ -241,7 +264,7 @@ __device__ __forceinline__ C halo_below(const C (&a)[P], const T* row, int k0, i
 template <typename T, typename C, int P>
 __device__ __forceinline__ C halo_above(const C (&a)[P], const T* row, int k0, int kb, int KB, int lane,
                                         bool split, float sc) {
-  C above = __shfl_down_sync(0xffffffffu, a[0], 1);
+  C above = shfl_down_c(a[0]);
   if (split && lane == 31 && kb < KB - 1) above = VecIO<T>::ld1(row + k0 + P, sc);
   return kb == KB - 1 ? C(0) : above;
 }

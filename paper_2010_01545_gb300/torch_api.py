@@ -14,7 +14,7 @@ from torch.autograd.function import once_differentiable
 from . import _abi
 
 _DTYPES = {"f64": (_abi.ADVECT_F64, torch.float64), "f32": (_abi.ADVECT_F32, torch.float32),
-           "f16s": (_abi.ADVECT_F16S, torch.float16)}
+           "f16s": (_abi.ADVECT_F16S, torch.float16), "f64ff": (_abi.ADVECT_F64_FF, torch.float64)}
 
 
 def coefficients_from_grid(grid):

@@ -1,0 +1,65 @@
+"""The FP64-accurate double-float mode (ADVECT_F64_FF): binary64 in memory,
+pairs of binary32 on the binary32 pipes.  It must meet the FP64 parity bar
+against the oracle (normwise 1e-12 per field) for the forward and the
+adjoint, on the sweep and the point kernels, and over a wide dynamic range."""
+import numpy as np
+import pytest
+
+import workload
+from gpu_util import dev, host, make_op, normwise, oracle_adjoint, oracle_forward
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(64, 64, 64), (33, 17, 65), (130, 66, 20), (5, 7, 3), (1, 1, 4), (16, 32, 128)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_ff_forward_meets_the_fp64_bar(shape):
+    op, grid = make_op(shape, "f64ff")
+    x = workload.winds(*shape, seed=41)
+    out = op.forward(*(dev(a) for a in x))
+    ref = oracle_forward(*x, grid)
+    for g, r, name in zip(out, ref, ("su", "sv", "sw")):
+        err = normwise(host(g), r)
+        assert err <= 1e-12, f"{name} {err:.2e} ({op.kernel_name()})"
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_ff_adjoint_meets_the_fp64_bar(shape):
+    op, grid = make_op(shape, "f64ff")
+    x = workload.winds(*shape, seed=42)
+    lam = workload.cotangents(*shape, seed=43)
+    g = op.adjoint(*(dev(a) for a in (*x, *lam)))
+    ref = oracle_adjoint(*x, *lam, grid)
+    for t, r, name in zip(g, ref, ("du", "dv", "dw")):
+        err = normwise(host(t), r)
+        assert err <= 1e-12, f"{name} {err:.2e} ({op.kernel_name(True)})"
+
+
+def test_ff_wide_dynamic_range():
+    """Fields scaled by factors from 1e-6 to 1e6 across x-planes."""
+    shape = (40, 24, 64)
+    op, grid = make_op(shape, "f64ff")
+    scale = 10.0 ** np.linspace(-6, 6, shape[0])[:, None, None]
+    x = [a * scale for a in workload.winds(*shape, seed=44)]
+    out = op.forward(*(dev(a) for a in x))
+    ref = oracle_forward(*x, grid)
+    for g, r in zip(out, ref):
+        assert normwise(host(g), r) <= 1e-12
+    # plane by plane the relative error stays small where the planes are small
+    su = host(out[0])
+    for i in (0, 5, 20):
+        m = np.max(np.abs(ref[0][i]))
+        assert np.max(np.abs(su[i] - ref[0][i])) <= 1e-11 * m
+
+
+def test_ff_sweep_configs(monkeypatch):
+    shape = (37, 45, 64)
+    x = workload.winds(*shape, seed=45)
+    for cfg in [(4, 64, 7, 3), (2, 5, 4, 1), (4, 300, 6, 1)]:
+        monkeypatch.setenv("ADVECT_SWEEP", ",".join(map(str, cfg)))
+        op, grid = make_op(shape, "f64ff")
+        assert op.kernel_name() == "fwd_sweep"
+        out = op.forward(*(dev(a) for a in x))
+        for g, r in zip(out, oracle_forward(*x, grid)):
+            assert normwise(host(g), r) <= 1e-12, cfg
