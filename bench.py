@@ -340,9 +340,12 @@ def run_e2e(args, torch, op, winds, world, n_pts):
     for _ in range(e2e_steps):
         op.forward_host(*h_in, h_out)
     e2e_secs = (time.perf_counter() - t0) / e2e_steps
+    link = 343.0  # GB/s, concurrent pinned H2D + D2H measured on this machine's GB300
     return {"value": world * n_pts / e2e_secs, "unit": UNIT,
             "h2d_bytes_per_step": 3 * n_pts * 8, "d2h_bytes_per_step": 3 * n_pts * 8,
-            "ms_per_step": 1e3 * e2e_secs}
+            "ms_per_step": 1e3 * e2e_secs,
+            "link_bound_ms": 6 * n_pts * 8 / link / 1e6,
+            "link_frac": (6 * n_pts * 8 / link / 1e6) / (1e3 * e2e_secs)}
 
 
 def run_case(args):

@@ -101,14 +101,17 @@ __device__ bool adjoint_tile(const Tile<T>& t, const Ring& R, int* flag) {
     const int o_l0 = off(3, 0), o_lym = off(3, -1), o_lyp = off(3, 1);
     const int o_m0 = off(4, 0), o_mym = off(4, -1), o_myp = off(4, 1);
     const int o_n0 = off(5, 0), o_nym = off(5, -1), o_nyp = off(5, 1);
-    auto slot_ptr = [&](int ql) -> const T* {
-      return reinterpret_cast<const T*>(R.slots + (size_t)(ql % R.nb) * R.slot_cap);
+    auto slot_ptr = [&](SlotPos q) -> const T* {
+      return reinterpret_cast<const T*>(R.slots + (size_t)q.slot * R.slot_cap);
     };
     int timed_out = 0;
-    auto wait = [&](int ql) {
-      if (!wait_plane(R, ql, flag, t.wait_budget)) timed_out = 1;
+    auto wait = [&](SlotPos q) {
+      if (!wait_plane(R, q, flag, t.wait_budget)) timed_out = 1;
     };
-    auto release = [&](int ql) { release_plane<6>(t, R, ql, nplanes, nwarps, lane); };
+    auto release = [&](int ql, SlotPos q) { release_plane<6>(t, R, ql, q, nplanes, nwarps, lane); };
+    const SlotPos q0{0, 0};
+    SlotPos q1{0, 0};
+    q1.next(R.nb);
     // cotangent masks: lu, lv live on k >= 1; lw on 1 <= k <= nz-2
     auto muv = [&](int k) { return k >= 1; };
     auto mw = [&](int k) { return k >= 1 && k <= nz - 2; };
@@ -144,11 +147,11 @@ __device__ bool adjoint_tile(const Tile<T>& t, const Ring& R, int* flag) {
     C LUM[P], LU0[P], LUMYP[P], LVM[P], LV0[P], LVYM[P], LWM[P], LW0[P];
     C u0P, umP, v0P, vymP, w0M, w0P, lu0M, lu0P, lumP, lv0M, lv0P, lvymP, lw0M, lw0P;
 
-    wait(0);
-    wait(1);
+    wait(q0);
+    wait(q1);
     {
-      const T* A = slot_ptr(0);
-      const T* B = slot_ptr(1);
+      const T* A = slot_ptr(q0);
+      const T* B = slot_ptr(q1);
       IO::ld(A + o_u0, UM);
       IO::ld(B + o_u0, U0);
       IO::ld(A + o_uyp, UMYP);
@@ -178,7 +181,9 @@ __device__ bool adjoint_tile(const Tile<T>& t, const Ring& R, int* flag) {
       lw0M = halo_below<T, C, P>(LW0, B + o_n0 - k0, k0, kb, lane, split, one);
       lw0P = halo_above<T, C, P>(LW0, B + o_n0 - k0, k0, kb, KB, lane, split, one);
     }
-    release(0);
+    release(0, q0);
+    SlotPos pc = q1, pn = q1;
+    pn.next(R.nb);
     mask_uv(LUM);
     mask_uv(LU0);
     mask_uv(LUMYP);
@@ -192,12 +197,11 @@ __device__ bool adjoint_tile(const Tile<T>& t, const Ring& R, int* flag) {
     if (!hp_w) lw0P = C(0);
 
     for (int i = t.i_lo; i < t.i_hi; ++i) {
-      const int qn = i - t.i_lo + 2;
-      const int qc = qn - 1;
-      wait(qn);
+      const int qc = i - t.i_lo + 1;
+      wait(pn);
       if (__any_sync(0xffffffffu, timed_out)) break;
-      const T* Pc = slot_ptr(qc);
-      const T* Pn = slot_ptr(qn);
+      const T* Pc = slot_ptr(pc);
+      const T* Pn = slot_ptr(pn);
       C UP[P], UYP[P], VP[P], VYP[P], VPYM[P], WP[P], WYP[P];
       C LUP[P], LUYM[P], LUYP[P], LVP[P], LVYP[P], LVPYM[P], LWP[P], LWYM[P], LWYP[P];
       IO::ld(Pn + o_u0, UP);
@@ -230,7 +234,9 @@ __device__ bool adjoint_tile(const Tile<T>& t, const Ring& R, int* flag) {
       C lwpP = halo_above<T, C, P>(LWP, Pn + o_n0 - k0, k0, kb, KB, lane, split, one);
       const C lvpymP = halo_above<T, C, P>(LVPYM, Pn + o_mym - k0, k0, kb, KB, lane, split, one);
       C lwypM = halo_below<T, C, P>(LWYP, Pc + o_nyp - k0, k0, kb, lane, split, one);
-      release(qc);
+      release(qc, pc);
+      pc = pn;
+      pn.next(R.nb);
       mask_uv(LUP);
       mask_uv(LUYM);
       mask_uv(LUYP);

@@ -27,7 +27,7 @@ struct HostPath {
   void* d_out[3] = {nullptr, nullptr, nullptr};
   cudaStream_t s_in = nullptr, s_k = nullptr, s_out = nullptr;
   static constexpr int kMaxChunks = 16;
-  int nchunk = 8;
+  int nchunk = 16;
   cudaEvent_t ev_in[kMaxChunks] = {};
   cudaEvent_t ev_k[kMaxChunks] = {};
 };

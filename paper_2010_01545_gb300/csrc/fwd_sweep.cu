@@ -16,7 +16,7 @@ struct SweepParams {
   int* flag;
 };
 
-template <typename T, int OCC>
+template <typename T, int OCC, bool F64Z>
 __global__ void __launch_bounds__(OCC == 1 ? 256 : 128, OCC) fwd_sweep_kernel(SweepParams p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const sweep::Ring R = sweep::make_ring(smem_raw, p.nb, p.slot_cap);
@@ -41,21 +41,28 @@ __global__ void __launch_bounds__(OCC == 1 ? 256 : 128, OCC) fwd_sweep_kernel(Sw
   t.f64_levels = p.a.f64_levels;
   t.wait_budget = p.a.wait_budget;
   t.skip_plane = p.a.skip_plane;
-  sweep::forward_tile<T>(t, R, p.flag);
+  sweep::forward_tile<T, F64Z>(t, R, p.flag);
 }
 
-template <typename T, int OCC>
+template <typename T, int OCC, bool F64Z = false>
 cudaError_t launch_occ(const SweepParams& p, dim3 grid, int threads, size_t smem, cudaStream_t st) {
   if (threads > (OCC == 1 ? 256 : 128)) return cudaErrorInvalidConfiguration;
   static int attr_bytes = -1;  // largest dynamic shared memory size already allowed
   if ((int)smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(fwd_sweep_kernel<T, OCC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(fwd_sweep_kernel<T, OCC, F64Z>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_bytes = (int)smem;
   }
-  fwd_sweep_kernel<T, OCC><<<grid, threads, smem, st>>>(p);
+  fwd_sweep_kernel<T, OCC, F64Z><<<grid, threads, smem, st>>>(p);
   return cudaGetLastError();
+}
+
+// Binary64 near-surface levels (F32/F16S only): one uncapped variant.
+template <typename T>
+cudaError_t launch_f64z(const SweepParams& p, dim3 grid, int threads, size_t smem, cudaStream_t st) {
+  if constexpr (sizeof(typename Store<T>::C) == 4) return launch_occ<T, 1, true>(p, grid, threads, smem, st);
+  return launch_occ<T, 1, false>(p, grid, threads, smem, st);
 }
 
 template <typename T>
@@ -72,6 +79,7 @@ cudaError_t launch_t(const FwdArgs& a, const SweepCfg& cfg, int* flag, cudaStrea
   const size_t smem = sweep_smem_bytes(a.s.nz, (int)sizeof(T), cfg);
   const dim3 grid((a.s.ny + cfg.ty - 1) / cfg.ty, (a.i1 - a.i0 + cfg.lx - 1) / cfg.lx);
   const int threads = cfg.ty * p.kb;
+  if (a.f64_levels > 0) return launch_f64z<T>(p, grid, threads, smem, st);
   switch (cfg.occ) {
     case 3: return launch_occ<T, 3>(p, grid, threads, smem, st);
     case 4: return launch_occ<T, 4>(p, grid, threads, smem, st);

@@ -155,8 +155,7 @@ struct Tile {
 // Bulk-copy plane ql of the tile (x index i_lo-1+ql, periodic) into its slot;
 // NF fields (t.nf == NF).
 template <int NF, typename T>
-__device__ __forceinline__ void issue_plane(const Tile<T>& t, const Ring& R, int ql) {
-  const int slot = ql % R.nb;
+__device__ __forceinline__ void issue_plane(const Tile<T>& t, const Ring& R, int ql, int slot) {
   int ig = t.i_lo - 1 + ql;
   ig = ig < 0 ? ig + t.nx : (ig >= t.nx ? ig - t.nx : ig);
   const int ty_eff = min(t.ty, t.ny - t.j0);
@@ -199,7 +198,7 @@ __device__ __forceinline__ void start_tile(const Tile<T>& t, const Ring& R, int 
   }
   __syncthreads();
   if (tid == 0) {
-    for (int q = 0; q < R.nb && q < nplanes; ++q) issue_plane<NF>(t, R, q);
+    for (int q = 0; q < R.nb && q < nplanes; ++q) issue_plane<NF>(t, R, q, q);
   }
 }
 
@@ -224,27 +223,37 @@ __device__ __forceinline__ bool finish_tile(const Ring& R, bool ok) {
 
 // Wait for plane ql of the tile; false (and the error flag raised) if the
 // bounded wait ran out.
-__device__ __forceinline__ bool wait_plane(const Ring& R, int ql, int* flag, long long budget) {
-  if (mbar_wait_bounded(&R.full[ql % R.nb], (uint32_t)((ql / R.nb) & 1), budget)) return true;
+// Plane ql of a tile sits in slot ql % NB and is that slot's (ql / NB)-th
+// use; sweeps advance these incrementally (no division in the loop).
+struct SlotPos {
+  int slot, use;
+  __device__ __forceinline__ void next(int nb) {
+    if (++slot == nb) {
+      slot = 0;
+      ++use;
+    }
+  }
+};
+
+__device__ __forceinline__ bool wait_plane(const Ring& R, SlotPos p, int* flag, long long budget) {
+  if (mbar_wait_bounded(&R.full[p.slot], (uint32_t)(p.use & 1), budget)) return true;
   atomicExch(flag, 1);
   return false;
 }
 
-// This warp is done reading plane ql's slot; the last of the tile's nwarps
-// warps to arrive issues the copy of plane ql + NB into it.
+// This warp is done reading plane ql (at position p); the last of the
+// tile's nwarps warps to arrive issues the copy of plane ql + NB into it.
 template <int NF, typename T>
-__device__ __forceinline__ void release_plane(const Tile<T>& t, const Ring& R, int ql, int nplanes, int nwarps,
-                                              int lane) {
+__device__ __forceinline__ void release_plane(const Tile<T>& t, const Ring& R, int ql, SlotPos p, int nplanes,
+                                              int nwarps, int lane) {
   __syncwarp();
   if (lane == 0) {
     __threadfence_block();
-    const int NB = R.nb;
-    const int target = (ql / NB + 1) * nwarps;
-    const int prev = atomicAdd(&R.arrived[ql % NB], 1);
-    if (prev + 1 == target && ql + NB < nplanes) {
+    const int prev = atomicAdd(&R.arrived[p.slot], 1);
+    if (prev + 1 == (p.use + 1) * nwarps && ql + R.nb < nplanes) {
       __threadfence_block();
       fence_proxy_async_smem();
-      issue_plane<NF>(t, R, ql + NB);
+      issue_plane<NF>(t, R, ql + R.nb, p.slot);
     }
   }
 }
@@ -273,7 +282,9 @@ __device__ __forceinline__ C halo_above(const C (&a)[P], const T* row, int k0, i
 // idle (no copy in flight, no thread reading it) on entry; on exit every copy
 // this call issued has completed or, after a timeout, been waited for with a
 // bounded budget.  Returns false if any wait of this thread's warp timed out.
-template <typename T>
+// F64Z: compile the binary64 near-surface branch (F32/F16S with
+// f64_levels > 0); the default instantiation has no binary64 code at all.
+template <typename T, bool F64Z = false>
 __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
   using IO = VecIO<T>;
   using C = typename IO::C;
@@ -300,14 +311,17 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
     const int o_u0 = r * nz, o_um = (r - 1) * nz, o_up = (r + 1) * nz;
     const int o_v0 = (rows + r) * nz, o_vm = (rows + r - 1) * nz, o_vp = (rows + r + 1) * nz;
     const int o_w0 = (2 * rows + r) * nz, o_wm = (2 * rows + r - 1) * nz, o_wp = (2 * rows + r + 1) * nz;
-    auto slot_ptr = [&](int ql) -> const T* {
-      return reinterpret_cast<const T*>(R.slots + (size_t)(ql % NB) * R.slot_cap);
+    auto slot_ptr = [&](SlotPos q) -> const T* {
+      return reinterpret_cast<const T*>(R.slots + (size_t)q.slot * R.slot_cap);
     };
     int timed_out = 0;
-    auto wait = [&](int ql) {
-      if (!wait_plane(R, ql, flag, t.wait_budget)) timed_out = 1;
+    auto wait = [&](SlotPos q) {
+      if (!wait_plane(R, q, flag, t.wait_budget)) timed_out = 1;
     };
-    auto release = [&](int ql) { release_plane<3>(t, R, ql, nplanes, nwarps, lane); };
+    auto release = [&](int ql, SlotPos q) { release_plane<3>(t, R, ql, q, nplanes, nwarps, lane); };
+    const SlotPos q0{0, 0};
+    SlotPos q1{0, 0};
+    q1.next(NB);
 
     C c1[P], c2[P], d1[P], d2[P];
 #pragma unroll
@@ -323,11 +337,11 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
     C UXM[P], U0[P], UXMYP[P], VXM[P], V0[P], VYM[P], WXM[P], W0[P];
     C SXm[P], SVm[P], SWm[P];
     C u0m, u0p, uxmp, v0m, v0p, vymp, w0m, w0p;
-    wait(0);
-    wait(1);
+    wait(q0);
+    wait(q1);
     {
-      const T* P0 = slot_ptr(0);
-      const T* P1 = slot_ptr(1);
+      const T* P0 = slot_ptr(q0);
+      const T* P1 = slot_ptr(q1);
       IO::ld(P0 + o_u0 + k0, s_u, UXM);
       IO::ld(P1 + o_u0 + k0, s_u, U0);
       IO::ld(P0 + o_up + k0, s_u, UXMYP);
@@ -345,7 +359,9 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
       w0m = halo_below<T, C, P>(W0, P1 + o_w0, k0, kb, lane, split, s_w);
       w0p = halo_above<T, C, P>(W0, P1 + o_w0, k0, kb, KB, lane, split, s_w);
     }
-    release(0);
+    release(0, q0);
+    SlotPos pc = q1, pn = q1;  // planes i and i+1
+    pn.next(NB);
 #pragma unroll
     for (int q = 0; q < P; ++q) {
       SXm[q] = UXM[q] + U0[q];
@@ -355,12 +371,11 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
     const bool f64z = sizeof(C) == 4 && t.f64_levels > 0 && k0 <= t.f64_levels;
 
     for (int i = t.i_lo; i < t.i_hi; ++i) {
-      const int qn = i - t.i_lo + 2;  // plane i+1
-      const int qc = qn - 1;          // plane i
-      wait(qn);
+      const int qc = i - t.i_lo + 1;  // plane i (plane i+1 is qc + 1)
+      wait(pn);
       if (__any_sync(0xffffffffu, timed_out)) break;
-      const T* Pc = slot_ptr(qc);
-      const T* Pn = slot_ptr(qn);
+      const T* Pc = slot_ptr(pc);
+      const T* Pn = slot_ptr(pn);
       C UXP[P], UYM[P], UYP[P], VXP[P], VYP[P], VXPYM[P], WXP[P], WYM[P], WYP[P];
       IO::ld(Pn + o_u0 + k0, s_u, UXP);
       IO::ld(Pc + o_um + k0, s_u, UYM);
@@ -380,7 +395,9 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
       const C vxpymp = halo_above<T, C, P>(VXPYM, Pn + o_vm, k0, kb, KB, lane, split, s_v);
       const C wypm = halo_below<T, C, P>(WYP, Pc + o_wp, k0, kb, lane, split, s_w);
       // plane i is no longer read from shared memory by this warp
-      release(qc);
+      release(qc, pc);
+      pc = pn;
+      pn.next(NB);
 
       C ou[P], ov[P], ow[P];
       C wu_lo = w0m + wxpm;   // w(i,k-1) + w(i+1,k-1): lower face of the u cell
@@ -414,7 +431,7 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
         C hv = tcx * xv + tcy * yv;
         C hw = tcx * xw + tcy * yw;
         const int k = k0 + q;
-        if (f64z && k >= 1 && k <= t.f64_levels) {
+        if (F64Z && f64z && k >= 1 && k <= t.f64_levels) {
           const double* dt = t.c.d;
           const double e1 = dt[k], e2 = dt[nz + k], e3 = dt[2 * nz + k], e4 = dt[3 * nz + k];
           hu = (C)((double)hu + e1 * (double)uzm * (double)wu_lo - e2 * (double)uzp * (double)wu_hi);
