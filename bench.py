@@ -232,6 +232,7 @@ def main():
                     help="nx,ny,nz of a smaller forward case (profiling); not a bench line")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "f16s", "f64ff"],
                     help="element type of the --shape case")
+    ap.add_argument("--adjoint", action="store_true", help="--shape case runs the adjoint")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -368,14 +369,19 @@ def run_case(args):
     else:
         d = [torch.from_numpy(a).to("cuda", op.torch_dtype) for a in winds]
     out = [op.empty() for _ in range(3)]
+    if args.adjoint:
+        lam = [torch.from_numpy(a).to("cuda", op.torch_dtype) for a in workload.cotangents(*shape)]
+        call = lambda: op.adjoint(*d, *lam, out=out)  # noqa: E731
+    else:
+        call = lambda: op.forward(*d, out=out, scales=scales)  # noqa: E731
     for _ in range(args.warmup):
-        op.forward(*d, out=out, scales=scales)
-    secs = time_calls(lambda: op.forward(*d, out=out, scales=scales), args.steps,
-                      torch.cuda.current_stream()) / args.steps
-    print(json.dumps({"case": f"fwd_{args.dtype}_{shape[0]}x{shape[1]}x{shape[2]}",
-                      "kernel": op.kernel_name(), "tile": op.tuned_config(), "ms": 1e3 * secs,
-                      "points_per_s": n_pts / secs, "steps": args.steps, "warmup": args.warmup}),
-          flush=True)
+        call()
+    secs = time_calls(call, args.steps, torch.cuda.current_stream()) / args.steps
+    kind = "adj" if args.adjoint else "fwd"
+    print(json.dumps({"case": f"{kind}_{args.dtype}_{shape[0]}x{shape[1]}x{shape[2]}",
+                      "kernel": op.kernel_name(args.adjoint), "tile": op.tuned_config(args.adjoint),
+                      "ms": 1e3 * secs, "points_per_s": n_pts / secs, "steps": args.steps,
+                      "warmup": args.warmup}), flush=True)
     return 0
 
 

@@ -72,7 +72,7 @@ struct AdjIO<f64ff> {
   }
 };
 
-template <typename T>
+template <typename T, bool SPLIT = true>
 __device__ bool adjoint_tile(const Tile<T>& t, const Ring& R, int* flag) {
   using IO = AdjIO<T>;
   using C = typename IO::C;
@@ -91,7 +91,6 @@ __device__ bool adjoint_tile(const Tile<T>& t, const Ring& R, int* flag) {
     const int k0 = kb * P;
     const int j = t.j0 + rr;
     const bool row_ok = j < ny;
-    const bool split = (32 % KB) != 0;
     const int r = rr + 1;
     // row offsets of field f, row r + d within a slot
     auto off = [&](int f, int d) { return (f * rows + r + d) * nz + k0; };
@@ -166,20 +165,20 @@ __device__ bool adjoint_tile(const Tile<T>& t, const Ring& R, int* flag) {
       IO::ld(B + o_mym, LVYM);
       IO::ld(A + o_n0, LWM);
       IO::ld(B + o_n0, LW0);
-      u0P = halo_above<T, C, P>(U0, B + o_u0 - k0, k0, kb, KB, lane, split, one);
-      umP = halo_above<T, C, P>(UM, A + o_u0 - k0, k0, kb, KB, lane, split, one);
-      v0P = halo_above<T, C, P>(V0, B + o_v0 - k0, k0, kb, KB, lane, split, one);
-      vymP = halo_above<T, C, P>(VYM, B + o_vym - k0, k0, kb, KB, lane, split, one);
-      w0M = halo_below<T, C, P>(W0, B + o_w0 - k0, k0, kb, lane, split, one);
-      w0P = halo_above<T, C, P>(W0, B + o_w0 - k0, k0, kb, KB, lane, split, one);
-      lu0M = halo_below<T, C, P>(LU0, B + o_l0 - k0, k0, kb, lane, split, one);
-      lu0P = halo_above<T, C, P>(LU0, B + o_l0 - k0, k0, kb, KB, lane, split, one);
-      lumP = halo_above<T, C, P>(LUM, A + o_l0 - k0, k0, kb, KB, lane, split, one);
-      lv0M = halo_below<T, C, P>(LV0, B + o_m0 - k0, k0, kb, lane, split, one);
-      lv0P = halo_above<T, C, P>(LV0, B + o_m0 - k0, k0, kb, KB, lane, split, one);
-      lvymP = halo_above<T, C, P>(LVYM, B + o_mym - k0, k0, kb, KB, lane, split, one);
-      lw0M = halo_below<T, C, P>(LW0, B + o_n0 - k0, k0, kb, lane, split, one);
-      lw0P = halo_above<T, C, P>(LW0, B + o_n0 - k0, k0, kb, KB, lane, split, one);
+      u0P = halo_above<SPLIT, T, C, P>(U0, B + o_u0 - k0, k0, kb, KB, lane, one);
+      umP = halo_above<SPLIT, T, C, P>(UM, A + o_u0 - k0, k0, kb, KB, lane, one);
+      v0P = halo_above<SPLIT, T, C, P>(V0, B + o_v0 - k0, k0, kb, KB, lane, one);
+      vymP = halo_above<SPLIT, T, C, P>(VYM, B + o_vym - k0, k0, kb, KB, lane, one);
+      w0M = halo_below<SPLIT, T, C, P>(W0, B + o_w0 - k0, k0, kb, lane, one);
+      w0P = halo_above<SPLIT, T, C, P>(W0, B + o_w0 - k0, k0, kb, KB, lane, one);
+      lu0M = halo_below<SPLIT, T, C, P>(LU0, B + o_l0 - k0, k0, kb, lane, one);
+      lu0P = halo_above<SPLIT, T, C, P>(LU0, B + o_l0 - k0, k0, kb, KB, lane, one);
+      lumP = halo_above<SPLIT, T, C, P>(LUM, A + o_l0 - k0, k0, kb, KB, lane, one);
+      lv0M = halo_below<SPLIT, T, C, P>(LV0, B + o_m0 - k0, k0, kb, lane, one);
+      lv0P = halo_above<SPLIT, T, C, P>(LV0, B + o_m0 - k0, k0, kb, KB, lane, one);
+      lvymP = halo_above<SPLIT, T, C, P>(LVYM, B + o_mym - k0, k0, kb, KB, lane, one);
+      lw0M = halo_below<SPLIT, T, C, P>(LW0, B + o_n0 - k0, k0, kb, lane, one);
+      lw0P = halo_above<SPLIT, T, C, P>(LW0, B + o_n0 - k0, k0, kb, KB, lane, one);
     }
     release(0, q0);
     SlotPos pc = q1, pn = q1;
@@ -220,20 +219,20 @@ __device__ bool adjoint_tile(const Tile<T>& t, const Ring& R, int* flag) {
       IO::ld(Pn + o_n0, LWP);
       IO::ld(Pc + o_nym, LWYM);
       IO::ld(Pc + o_nyp, LWYP);
-      const C upP = halo_above<T, C, P>(UP, Pn + o_u0 - k0, k0, kb, KB, lane, split, one);
-      const C vpP = halo_above<T, C, P>(VP, Pn + o_v0 - k0, k0, kb, KB, lane, split, one);
-      const C wpM = halo_below<T, C, P>(WP, Pn + o_w0 - k0, k0, kb, lane, split, one);
-      const C wpP = halo_above<T, C, P>(WP, Pn + o_w0 - k0, k0, kb, KB, lane, split, one);
-      const C vpymP = halo_above<T, C, P>(VPYM, Pn + o_vym - k0, k0, kb, KB, lane, split, one);
-      const C wypM = halo_below<T, C, P>(WYP, Pc + o_wyp - k0, k0, kb, lane, split, one);
-      C lupM = halo_below<T, C, P>(LUP, Pn + o_l0 - k0, k0, kb, lane, split, one);
-      C lupP = halo_above<T, C, P>(LUP, Pn + o_l0 - k0, k0, kb, KB, lane, split, one);
-      C lvpM = halo_below<T, C, P>(LVP, Pn + o_m0 - k0, k0, kb, lane, split, one);
-      C lvpP = halo_above<T, C, P>(LVP, Pn + o_m0 - k0, k0, kb, KB, lane, split, one);
-      C lwpM = halo_below<T, C, P>(LWP, Pn + o_n0 - k0, k0, kb, lane, split, one);
-      C lwpP = halo_above<T, C, P>(LWP, Pn + o_n0 - k0, k0, kb, KB, lane, split, one);
-      const C lvpymP = halo_above<T, C, P>(LVPYM, Pn + o_mym - k0, k0, kb, KB, lane, split, one);
-      C lwypM = halo_below<T, C, P>(LWYP, Pc + o_nyp - k0, k0, kb, lane, split, one);
+      const C upP = halo_above<SPLIT, T, C, P>(UP, Pn + o_u0 - k0, k0, kb, KB, lane, one);
+      const C vpP = halo_above<SPLIT, T, C, P>(VP, Pn + o_v0 - k0, k0, kb, KB, lane, one);
+      const C wpM = halo_below<SPLIT, T, C, P>(WP, Pn + o_w0 - k0, k0, kb, lane, one);
+      const C wpP = halo_above<SPLIT, T, C, P>(WP, Pn + o_w0 - k0, k0, kb, KB, lane, one);
+      const C vpymP = halo_above<SPLIT, T, C, P>(VPYM, Pn + o_vym - k0, k0, kb, KB, lane, one);
+      const C wypM = halo_below<SPLIT, T, C, P>(WYP, Pc + o_wyp - k0, k0, kb, lane, one);
+      C lupM = halo_below<SPLIT, T, C, P>(LUP, Pn + o_l0 - k0, k0, kb, lane, one);
+      C lupP = halo_above<SPLIT, T, C, P>(LUP, Pn + o_l0 - k0, k0, kb, KB, lane, one);
+      C lvpM = halo_below<SPLIT, T, C, P>(LVP, Pn + o_m0 - k0, k0, kb, lane, one);
+      C lvpP = halo_above<SPLIT, T, C, P>(LVP, Pn + o_m0 - k0, k0, kb, KB, lane, one);
+      C lwpM = halo_below<SPLIT, T, C, P>(LWP, Pn + o_n0 - k0, k0, kb, lane, one);
+      C lwpP = halo_above<SPLIT, T, C, P>(LWP, Pn + o_n0 - k0, k0, kb, KB, lane, one);
+      const C lvpymP = halo_above<SPLIT, T, C, P>(LVPYM, Pn + o_mym - k0, k0, kb, KB, lane, one);
+      C lwypM = halo_below<SPLIT, T, C, P>(LWYP, Pc + o_nyp - k0, k0, kb, lane, one);
       release(qc, pc);
       pc = pn;
       pn.next(R.nb);

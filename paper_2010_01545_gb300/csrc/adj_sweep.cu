@@ -11,7 +11,7 @@ struct AdjParams {
   int* flag;
 };
 
-template <typename T, int OCC>
+template <typename T, int OCC, bool SPLIT>
 __global__ void __launch_bounds__(OCC == 1 ? 256 : 128, OCC) adj_sweep_kernel(AdjParams p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const sweep::Ring R = sweep::make_ring(smem_raw, p.nb, p.slot_cap);
@@ -42,21 +42,27 @@ __global__ void __launch_bounds__(OCC == 1 ? 256 : 128, OCC) adj_sweep_kernel(Ad
   t.f64_levels = 0;
   t.wait_budget = p.a.wait_budget;
   t.skip_plane = p.a.skip_plane;
-  sweep::adjoint_tile<T>(t, R, p.flag);
+  sweep::adjoint_tile<T, SPLIT>(t, R, p.flag);
+}
+
+template <typename T, int OCC, bool SPLIT>
+cudaError_t launch_v(const AdjParams& p, dim3 grid, int threads, size_t smem, cudaStream_t st) {
+  if (threads > (OCC == 1 ? 256 : 128)) return cudaErrorInvalidConfiguration;
+  static int attr_bytes = -1;
+  if ((int)smem > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(adj_sweep_kernel<T, OCC, SPLIT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_bytes = (int)smem;
+  }
+  adj_sweep_kernel<T, OCC, SPLIT><<<grid, threads, smem, st>>>(p);
+  return cudaGetLastError();
 }
 
 template <typename T, int OCC>
 cudaError_t launch_occ(const AdjParams& p, dim3 grid, int threads, size_t smem, cudaStream_t st) {
-  if (threads > (OCC == 1 ? 256 : 128)) return cudaErrorInvalidConfiguration;
-  static int attr_bytes = -1;
-  if ((int)smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(adj_sweep_kernel<T, OCC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_bytes = (int)smem;
-  }
-  adj_sweep_kernel<T, OCC><<<grid, threads, smem, st>>>(p);
-  return cudaGetLastError();
+  if (32 % p.kb != 0) return launch_v<T, OCC, true>(p, grid, threads, smem, st);
+  return launch_v<T, OCC, false>(p, grid, threads, smem, st);
 }
 
 template <typename T>

@@ -53,7 +53,7 @@ struct EnsParams {
 
 constexpr int kEnsThreads = 128;
 
-template <typename T, int OCC, int ADJ>
+template <typename T, int OCC, int ADJ, bool SPLIT>
 __global__ void __launch_bounds__(kEnsThreads, OCC) ens_kernel(EnsParams p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int s_tile;
@@ -95,7 +95,8 @@ __global__ void __launch_bounds__(kEnsThreads, OCC) ens_kernel(EnsParams p) {
       t.sc.inv_out[q] = 1.f;
     }
     t.f64_levels = 0;
-    const bool ok = ADJ ? sweep::adjoint_tile<T>(t, R, p.flag) : sweep::forward_tile<T>(t, R, p.flag);
+    const bool ok = ADJ ? sweep::adjoint_tile<T, SPLIT>(t, R, p.flag)
+                        : sweep::forward_tile<T, false, SPLIT>(t, R, p.flag);
     if (!ok) break;  // uniform across the CTA
   }
 }
@@ -115,16 +116,16 @@ int member_ty(int kb) {
 }
 
 template <typename T, int OCC, int ADJ>
-void* kernel_ptr() {
-  return (void*)ens_kernel<T, OCC, ADJ>;
+void* kernel_ptr(bool split) {
+  return split ? (void*)ens_kernel<T, OCC, ADJ, true> : (void*)ens_kernel<T, OCC, ADJ, false>;
 }
 
 template <typename T, int ADJ>
-void* kernel_for(int occ) {
+void* kernel_for(int occ, bool split) {
   switch (occ) {
-    case 4: return kernel_ptr<T, 4, ADJ>();
-    case 3: return kernel_ptr<T, 3, ADJ>();
-    default: return kernel_ptr<T, 2, ADJ>();
+    case 4: return kernel_ptr<T, 4, ADJ>(split);
+    case 3: return kernel_ptr<T, 3, ADJ>(split);
+    default: return kernel_ptr<T, 2, ADJ>(split);
   }
 }
 
@@ -138,6 +139,7 @@ struct EnsDir {  // one direction (forward or adjoint)
   std::vector<const void*> last_ptrs;
   int n_tiles = 0;
   size_t slot_cap = 0;
+  bool split = false;  // some member's rows straddle warps
   EnsCfg cfg{64, 6, 4};
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
@@ -161,6 +163,7 @@ static void build_table(const advect_ctx& ctx, EnsState& st, int adj, const void
   std::vector<MemberDesc<T>> v(n);
   int tile = 0;
   size_t cap = 0;
+  bool split = false;
   const int P = vec_of<T>(adj != 0);
   for (int r = 0; r < n; ++r) {
     const int m = st.order[r];
@@ -185,7 +188,9 @@ static void build_table(const advect_ctx& ctx, EnsState& st, int adj, const void
     d.c.tcx_f = (float)mm.tcx;
     d.c.tcy_f = (float)mm.tcy;
     cap = std::max(cap, (size_t)(adj ? 6 : 3) * (d.ty + 2) * mm.nz * sizeof(T));
+    split = split || (32 % d.kb) != 0;
   }
+  D.split = split;
   D.n_tiles = tile;
   D.slot_cap = (cap + 127) / 128 * 128;
   D.host_desc.resize(v.size() * sizeof(MemberDesc<T>));
@@ -283,7 +288,7 @@ static cudaError_t ens_run_t(advect_ctx& ctx, EnsState& st, int adj, const EnsCf
                                     stream);
     if (e != cudaSuccess) return e;
   }
-  void* fn = adj ? kernel_for<T, 1>(cfg.occ) : kernel_for<T, 0>(cfg.occ);
+  void* fn = adj ? kernel_for<T, 1>(cfg.occ, D.split) : kernel_for<T, 0>(cfg.occ, D.split);
   const size_t smem = ens_smem_bytes(st, adj, cfg);
   cudaError_t e = set_smem_attr(fn, smem);
   if (e != cudaSuccess) return e;

@@ -16,7 +16,7 @@ struct SweepParams {
   int* flag;
 };
 
-template <typename T, int OCC, bool F64Z>
+template <typename T, int OCC, bool F64Z, bool SPLIT>
 __global__ void __launch_bounds__(OCC == 1 ? 256 : 128, OCC) fwd_sweep_kernel(SweepParams p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const sweep::Ring R = sweep::make_ring(smem_raw, p.nb, p.slot_cap);
@@ -41,21 +41,27 @@ __global__ void __launch_bounds__(OCC == 1 ? 256 : 128, OCC) fwd_sweep_kernel(Sw
   t.f64_levels = p.a.f64_levels;
   t.wait_budget = p.a.wait_budget;
   t.skip_plane = p.a.skip_plane;
-  sweep::forward_tile<T, F64Z>(t, R, p.flag);
+  sweep::forward_tile<T, F64Z, SPLIT>(t, R, p.flag);
 }
 
-template <typename T, int OCC, bool F64Z = false>
-cudaError_t launch_occ(const SweepParams& p, dim3 grid, int threads, size_t smem, cudaStream_t st) {
+template <typename T, int OCC, bool F64Z, bool SPLIT>
+cudaError_t launch_v(const SweepParams& p, dim3 grid, int threads, size_t smem, cudaStream_t st) {
   if (threads > (OCC == 1 ? 256 : 128)) return cudaErrorInvalidConfiguration;
   static int attr_bytes = -1;  // largest dynamic shared memory size already allowed
   if ((int)smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(fwd_sweep_kernel<T, OCC, F64Z>,
+    cudaError_t e = cudaFuncSetAttribute(fwd_sweep_kernel<T, OCC, F64Z, SPLIT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_bytes = (int)smem;
   }
-  fwd_sweep_kernel<T, OCC, F64Z><<<grid, threads, smem, st>>>(p);
+  fwd_sweep_kernel<T, OCC, F64Z, SPLIT><<<grid, threads, smem, st>>>(p);
   return cudaGetLastError();
+}
+
+template <typename T, int OCC, bool F64Z = false>
+cudaError_t launch_occ(const SweepParams& p, dim3 grid, int threads, size_t smem, cudaStream_t st) {
+  if (32 % p.kb != 0) return launch_v<T, OCC, F64Z, true>(p, grid, threads, smem, st);
+  return launch_v<T, OCC, F64Z, false>(p, grid, threads, smem, st);
 }
 
 // Binary64 near-surface levels (F32/F16S only): one uncapped variant.

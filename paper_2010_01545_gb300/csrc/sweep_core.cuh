@@ -262,19 +262,20 @@ __device__ __forceinline__ void release_plane(const Tile<T>& t, const Ring& R, i
 // (k0+P) the thread's levels, taken from the neighbouring lanes of the same
 // row; zero beyond the column; a shared-memory read where the row crosses a
 // warp boundary (only when a row spans more than one warp).
-template <typename T, typename C, int P>
-__device__ __forceinline__ C halo_below(const C (&a)[P], const T* row, int k0, int kb, int lane, bool split,
-                                        float sc) {
+// SPLIT (compile time): rows may straddle warps (32 is not a multiple of the
+// k-blocks per row); only then is the shared-memory fallback compiled.
+template <bool SPLIT, typename T, typename C, int P>
+__device__ __forceinline__ C halo_below(const C (&a)[P], const T* row, int k0, int kb, int lane, float sc) {
   C below = shfl_up_c(a[P - 1]);
-  if (split && lane == 0 && kb > 0) below = VecIO<T>::ld1(row + k0 - 1, sc);
+  if (SPLIT && lane == 0 && kb > 0) below = VecIO<T>::ld1(row + k0 - 1, sc);
   return kb == 0 ? C(0) : below;
 }
 
-template <typename T, typename C, int P>
+template <bool SPLIT, typename T, typename C, int P>
 __device__ __forceinline__ C halo_above(const C (&a)[P], const T* row, int k0, int kb, int KB, int lane,
-                                        bool split, float sc) {
+                                        float sc) {
   C above = shfl_down_c(a[0]);
-  if (split && lane == 31 && kb < KB - 1) above = VecIO<T>::ld1(row + k0 + P, sc);
+  if (SPLIT && lane == 31 && kb < KB - 1) above = VecIO<T>::ld1(row + k0 + P, sc);
   return kb == KB - 1 ? C(0) : above;
 }
 
@@ -284,7 +285,7 @@ __device__ __forceinline__ C halo_above(const C (&a)[P], const T* row, int k0, i
 // bounded budget.  Returns false if any wait of this thread's warp timed out.
 // F64Z: compile the binary64 near-surface branch (F32/F16S with
 // f64_levels > 0); the default instantiation has no binary64 code at all.
-template <typename T, bool F64Z = false>
+template <typename T, bool F64Z = false, bool SPLIT = true>
 __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
   using IO = VecIO<T>;
   using C = typename IO::C;
@@ -305,7 +306,6 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
     const int k0 = kb * P;
     const int j = t.j0 + rr;
     const bool row_ok = j < ny;
-    const bool split = (32 % KB) != 0;  // a row may straddle two warps
     const float s_u = t.sc.in[0], s_v = t.sc.in[1], s_w = t.sc.in[2];
     const int r = rr + 1;
     const int o_u0 = r * nz, o_um = (r - 1) * nz, o_up = (r + 1) * nz;
@@ -334,8 +334,14 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
     }
     const C tcx = S::tcx(t.c), tcy = S::tcy(t.c);
 
+    // Face sums shared with the previous plane: rolled in registers where the
+    // arithmetic is the bottleneck (binary64, double-float); recomputed (three
+    // adds per point) for binary32 arithmetic, where the 3P registers they
+    // would hold cost more than the adds.
+    constexpr bool kRoll = sizeof(C) != 4;
+    constexpr int PS = kRoll ? P : 1;
     C UXM[P], U0[P], UXMYP[P], VXM[P], V0[P], VYM[P], WXM[P], W0[P];
-    C SXm[P], SVm[P], SWm[P];
+    C SXm[PS], SVm[PS], SWm[PS];
     C u0m, u0p, uxmp, v0m, v0p, vymp, w0m, w0p;
     wait(q0);
     wait(q1);
@@ -350,23 +356,25 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
       IO::ld(P1 + o_vm + k0, s_v, VYM);
       IO::ld(P0 + o_w0 + k0, s_w, WXM);
       IO::ld(P1 + o_w0 + k0, s_w, W0);
-      u0m = halo_below<T, C, P>(U0, P1 + o_u0, k0, kb, lane, split, s_u);
-      u0p = halo_above<T, C, P>(U0, P1 + o_u0, k0, kb, KB, lane, split, s_u);
-      uxmp = halo_above<T, C, P>(UXM, P0 + o_u0, k0, kb, KB, lane, split, s_u);
-      v0m = halo_below<T, C, P>(V0, P1 + o_v0, k0, kb, lane, split, s_v);
-      v0p = halo_above<T, C, P>(V0, P1 + o_v0, k0, kb, KB, lane, split, s_v);
-      vymp = halo_above<T, C, P>(VYM, P1 + o_vm, k0, kb, KB, lane, split, s_v);
-      w0m = halo_below<T, C, P>(W0, P1 + o_w0, k0, kb, lane, split, s_w);
-      w0p = halo_above<T, C, P>(W0, P1 + o_w0, k0, kb, KB, lane, split, s_w);
+      u0m = halo_below<SPLIT, T, C, P>(U0, P1 + o_u0, k0, kb, lane, s_u);
+      u0p = halo_above<SPLIT, T, C, P>(U0, P1 + o_u0, k0, kb, KB, lane, s_u);
+      uxmp = halo_above<SPLIT, T, C, P>(UXM, P0 + o_u0, k0, kb, KB, lane, s_u);
+      v0m = halo_below<SPLIT, T, C, P>(V0, P1 + o_v0, k0, kb, lane, s_v);
+      v0p = halo_above<SPLIT, T, C, P>(V0, P1 + o_v0, k0, kb, KB, lane, s_v);
+      vymp = halo_above<SPLIT, T, C, P>(VYM, P1 + o_vm, k0, kb, KB, lane, s_v);
+      w0m = halo_below<SPLIT, T, C, P>(W0, P1 + o_w0, k0, kb, lane, s_w);
+      w0p = halo_above<SPLIT, T, C, P>(W0, P1 + o_w0, k0, kb, KB, lane, s_w);
     }
     release(0, q0);
     SlotPos pc = q1, pn = q1;  // planes i and i+1
     pn.next(NB);
+    if constexpr (kRoll) {
 #pragma unroll
-    for (int q = 0; q < P; ++q) {
-      SXm[q] = UXM[q] + U0[q];
-      SVm[q] = UXM[q] + UXMYP[q];
-      SWm[q] = UXM[q] + (q < P - 1 ? UXM[q + 1] : uxmp);
+      for (int q = 0; q < P; ++q) {
+        SXm[q] = UXM[q] + U0[q];
+        SVm[q] = UXM[q] + UXMYP[q];
+        SWm[q] = UXM[q] + (q < P - 1 ? UXM[q + 1] : uxmp);
+      }
     }
     const bool f64z = sizeof(C) == 4 && t.f64_levels > 0 && k0 <= t.f64_levels;
 
@@ -386,14 +394,14 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
       IO::ld(Pn + o_w0 + k0, s_w, WXP);
       IO::ld(Pc + o_wm + k0, s_w, WYM);
       IO::ld(Pc + o_wp + k0, s_w, WYP);
-      const C uxpm = halo_below<T, C, P>(UXP, Pn + o_u0, k0, kb, lane, split, s_u);
-      const C uxpp = halo_above<T, C, P>(UXP, Pn + o_u0, k0, kb, KB, lane, split, s_u);
-      const C vxpm = halo_below<T, C, P>(VXP, Pn + o_v0, k0, kb, lane, split, s_v);
-      const C vxpp = halo_above<T, C, P>(VXP, Pn + o_v0, k0, kb, KB, lane, split, s_v);
-      const C wxpm = halo_below<T, C, P>(WXP, Pn + o_w0, k0, kb, lane, split, s_w);
-      const C wxpp = halo_above<T, C, P>(WXP, Pn + o_w0, k0, kb, KB, lane, split, s_w);
-      const C vxpymp = halo_above<T, C, P>(VXPYM, Pn + o_vm, k0, kb, KB, lane, split, s_v);
-      const C wypm = halo_below<T, C, P>(WYP, Pc + o_wp, k0, kb, lane, split, s_w);
+      const C uxpm = halo_below<SPLIT, T, C, P>(UXP, Pn + o_u0, k0, kb, lane, s_u);
+      const C uxpp = halo_above<SPLIT, T, C, P>(UXP, Pn + o_u0, k0, kb, KB, lane, s_u);
+      const C vxpm = halo_below<SPLIT, T, C, P>(VXP, Pn + o_v0, k0, kb, lane, s_v);
+      const C vxpp = halo_above<SPLIT, T, C, P>(VXP, Pn + o_v0, k0, kb, KB, lane, s_v);
+      const C wxpm = halo_below<SPLIT, T, C, P>(WXP, Pn + o_w0, k0, kb, lane, s_w);
+      const C wxpp = halo_above<SPLIT, T, C, P>(WXP, Pn + o_w0, k0, kb, KB, lane, s_w);
+      const C vxpymp = halo_above<SPLIT, T, C, P>(VXPYM, Pn + o_vm, k0, kb, KB, lane, s_v);
+      const C wypm = halo_below<SPLIT, T, C, P>(WYP, Pc + o_wp, k0, kb, lane, s_w);
       // plane i is no longer read from shared memory by this warp
       release(qc, pc);
       pc = pn;
@@ -412,19 +420,29 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
         const C wzm = q > 0 ? W0[q - 1] : w0m;
         const C wzp = q < P - 1 ? W0[q + 1] : w0p;
         const C vym_zp = q < P - 1 ? VYM[q + 1] : vymp;
+        C sxm, svm, swm;  // face sums at x = i (shared with plane i-1)
+        if constexpr (kRoll) {
+          sxm = SXm[q];
+          svm = SVm[q];
+          swm = SWm[q];
+        } else {
+          sxm = UXM[q] + U0[q];
+          svm = UXM[q] + UXMYP[q];
+          swm = UXM[q] + (q < P - 1 ? UXM[q + 1] : uxmp);
+        }
         // su (Listing 1)
         const C sx = U0[q] + UXP[q];
-        const C xu = UXM[q] * SXm[q] - UXP[q] * sx;
+        const C xu = UXM[q] * sxm - UXP[q] * sx;
         const C yu = UYM[q] * (VYM[q] + VXPYM[q]) - UYP[q] * (V0[q] + VXP[q]);
         const C wu_hi = W0[q] + WXP[q];
         // sv
         const C sv_x = U0[q] + UYP[q];
-        const C xv = VXM[q] * SVm[q] - VXP[q] * sv_x;
+        const C xv = VXM[q] * svm - VXP[q] * sv_x;
         const C yv = VYM[q] * (V0[q] + VYM[q]) - VYP[q] * (V0[q] + VYP[q]);
         const C wv_hi = W0[q] + WYP[q];
         // sw
         const C sw_x = U0[q] + uzp;
-        const C xw = WXM[q] * SWm[q] - WXP[q] * sw_x;
+        const C xw = WXM[q] * swm - WXP[q] * sw_x;
         const C yw = WYM[q] * (VYM[q] + vym_zp) - WYP[q] * (V0[q] + vzp);
         const C ww_hi = W0[q] + wzp;
         C hu = tcx * xu + tcy * yu;
@@ -445,9 +463,11 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
         ou[q] = k >= 1 ? hu : C(0);
         ov[q] = k >= 1 ? hv : C(0);
         ow[q] = (k >= 1 && k < nz - 1) ? hw : C(0);
-        SXm[q] = sx;
-        SVm[q] = sv_x;
-        SWm[q] = sw_x;
+        if constexpr (kRoll) {
+          SXm[q] = sx;
+          SVm[q] = sv_x;
+          SWm[q] = sw_x;
+        }
         wu_lo = wu_hi;
         wv_lo = wv_hi;
         ww_lo = ww_hi;
