@@ -111,18 +111,17 @@ __device__ bool adjoint_tile(const Tile<T>& t, const Ring& R, int* flag) {
     const SlotPos q0{0, 0};
     SlotPos q1{0, 0};
     q1.next(R.nb);
-    // cotangent masks: lu, lv live on k >= 1; lw on 1 <= k <= nz-2
+    // cotangent masks: lu, lv live on k >= 1; lw on 1 <= k <= nz-2.  Only the
+    // first level of the column (q = 0 of k-block 0) and, for lw, the top
+    // level can be masked, so each vector needs at most two selects.
     auto muv = [&](int k) { return k >= 1; };
     auto mw = [&](int k) { return k >= 1 && k <= nz - 2; };
-    auto mask_uv = [&](C (&a)[P]) {
-#pragma unroll
-      for (int q = 0; q < P; ++q)
-        if (!muv(k0 + q)) a[q] = C(0);
-    };
+    const bool bottom = k0 == 0;                    // element 0 is level 0
+    const bool lid = k0 + P - 1 == nz - 1;          // element P-1 is the top level
+    auto mask_uv = [&](C (&a)[P]) { a[0] = bottom ? C(0) : a[0]; };
     auto mask_w = [&](C (&a)[P]) {
-#pragma unroll
-      for (int q = 0; q < P; ++q)
-        if (!mw(k0 + q)) a[q] = C(0);
+      a[0] = bottom ? C(0) : a[0];
+      a[P - 1] = lid ? C(0) : a[P - 1];
     };
     auto coef = [&](int table, int k) -> C { return (k < 0 || k >= nz) ? C(0) : S::coef(t.c, table, nz, k); };
     C c1u[P], c2d[P], c20[P], d10[P], d1u[P], d20[P], d2d[P];
@@ -279,22 +278,22 @@ __device__ bool adjoint_tile(const Tile<T>& t, const Ring& R, int* flag) {
         const C lwxp_zm = q > 0 ? LWP[q - 1] : lwpM;
         const C lwyp_zm = q > 0 ? LWYP[q - 1] : lwypM;
 
-        C a = tcx * (luxp * (uxp + u0 + u0) + lu0 * (uxm - uxp) - luxm * (uxm + u0 + u0));
+        const C u2 = u0 + u0, v2 = v0 + v0, w2 = w0 + w0;  // exact doublings
+        C a = tcx * (luxp * (uxp + u2) + lu0 * (uxm - uxp) - luxm * (uxm + u2));
         a += tcy * (luyp * (v0 + vxp) - luym * (vym + vym_xp));
         a += c1u[q] * luzp * (w0 + wxp) - c2d[q] * luzm * (wzm + wzm_xp);
         a += tcx * (lvxp * v0 + lvxp_ym * vym - lv0 * vxp - lvym * vym_xp);
         a += tcx * (lwxp * w0 + lwxp_zm * wzm - lw0 * wxp - lwzm * wzm_xp);
         C b = tcy * (luyp * u0 + luxm_yp * uxm - lu0 * uyp - luxm * uxm_yp);
         b += tcx * (lvxp * (u0 + uyp) - lvxm * (uxm + uxm_yp));
-        b += tcy * (lvyp * (vyp + v0 + v0) + lv0 * (vym - vyp) - lvym * (vym + v0 + v0));
+        b += tcy * (lvyp * (vyp + v2) + lv0 * (vym - vyp) - lvym * (vym + v2));
         b += c1u[q] * lvzp * (w0 + wyp) - c2d[q] * lvzm * (wzm + wzm_yp);
         b += tcy * (lwyp * w0 + lwyp_zm * wzm - lw0 * wyp - lwzm * wzm_yp);
         C c = c1u[q] * (luzp * u0 + luxm_zp * uxm + lvzp * v0 + lvym_zp * vym);
         c -= c20[q] * (lu0 * uzp + luxm * uxm_zp + lv0 * vzp + lvym * vym_zp);
         c += tcx * (lwxp * (u0 + uzp) - lwxm * (uxm + uxm_zp));
         c += tcy * (lwyp * (v0 + vzp) - lwym * (vym + vym_zp));
-        c += d1u[q] * lwzp * (wzp + w0 + w0) + lw0 * (d10[q] * wzm - d20[q] * wzp) -
-             d2d[q] * lwzm * (wzm + w0 + w0);
+        c += d1u[q] * lwzp * (wzp + w2) + lw0 * (d10[q] * wzm - d20[q] * wzp) - d2d[q] * lwzm * (wzm + w2);
         gu[q] = a;
         gv[q] = b;
         gw[q] = c;
