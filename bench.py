@@ -194,6 +194,21 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- GPU legs
+def whole_job_rate(local_units, local_seconds, device):
+    """Units of all ranks over the slowest rank's time (the timed regions are
+    bracketed by barriers, so the slowest rank bounds the job)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return local_units / local_seconds, local_seconds
+    t = torch.tensor([float(local_seconds), float(local_units)], dtype=torch.float64, device=device)
+    secs = t[:1].clone()
+    dist.all_reduce(secs, op=dist.ReduceOp.MAX)
+    units = t[1:].clone()
+    dist.all_reduce(units, op=dist.ReduceOp.SUM)
+    return units.item() / secs.item(), secs.item()
+
+
 def time_calls(fn, steps, stream):
     import torch
     e0 = torch.cuda.Event(enable_timing=True)
@@ -271,11 +286,7 @@ def main():
         dist.barrier()
     with ClockSampler(local) as clk:
         secs = time_calls(step, args.steps, stream)
-    if world > 1:
-        t = torch.tensor([secs], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        secs = t.item()
-    value = world * n_pts * args.steps / secs
+    value, secs = whole_job_rate(n_pts * args.steps, secs, "cuda")
     per_launch = secs / args.steps
     fwd_name = op.kernel_name()
 
