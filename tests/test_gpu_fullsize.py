@@ -103,3 +103,49 @@ def test_adjoint_f64_1024x1024x128_dot_product_and_probes():
         # probes away from the periodic seams see their whole neighbourhood
         if all(0 < c < n - 1 for c, n in zip(p[:2], shape[:2])):
             assert abs(fd - jt_h[f][p]) <= 1e-7 * (1 + abs(jt_h[f][p])), (f, p, fd, jt_h[f][p])
+
+
+def test_ensemble_48_members_as_benchmarked():
+    """The 48-member FP32 ensemble of the benchmark (autotuned, one persistent
+    launch per direction): every member's forward against the oracle on
+    sampled points, every member's adjoint bitwise against the single-grid
+    adjoint, and the three smallest members' adjoints fully against the
+    oracle."""
+    from gpu_util import ensure_built, lib_coeffs, oracle_adjoint
+    from paper_2010_01545_gb300 import torch_api
+    ensure_built()
+    shapes = workload.ensemble_shapes(48)
+    grids = [workload.vertical_grid(s[2]) for s in shapes]
+    coeffs = [lib_coeffs(g) for g in grids]
+    ens = torch_api.AdvectEnsemble(shapes, coeffs, "f32")
+    ens.autotune(True)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(workload.DEFAULT_SEED)
+    x = [[torch.rand(s, generator=gen, device="cuda") * 20 - 10 for s in shapes] for _ in range(3)]
+    lam = [[torch.randn(s, generator=gen, device="cuda") for s in shapes] for _ in range(3)]
+    y = ens.forward(*x)
+    g = ens.adjoint(*x, *lam)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(7)
+    for m, s in enumerate(shapes):
+        xm = [f[m].to(torch.float64).cpu().numpy() for f in x]
+        n = s[0] * s[1] * s[2]
+        idx = np.unique(np.concatenate([rng.integers(0, n, 1500), np.arange(s[2]), n - 1 - np.arange(s[2])]))
+        ref = oracle.forward_points(*xm, oracle.coefficients(grids[m]), idx)
+        for f in range(3):
+            got = y[f][m].reshape(-1)[torch.from_numpy(idx).cuda()].to(torch.float64).cpu().numpy()
+            err = np.max(np.abs(got - ref[:, f])) / max(np.max(np.abs(ref[:, f])), 1e-30)
+            assert err <= 2e-6, (m, s, f, err)
+        op = torch_api.Advect(*s, coeffs[m], "f32")
+        single = op.adjoint(*(f[m] for f in x), *(f[m] for f in lam))
+        for f in range(3):
+            assert torch.equal(g[f][m], single[f]), (m, s, f)
+        op.close()
+    for m in sorted(range(len(shapes)), key=lambda q: np.prod(shapes[q]))[:3]:
+        xm = [f[m].to(torch.float64).cpu().numpy() for f in x]
+        lm = [f[m].to(torch.float64).cpu().numpy() for f in lam]
+        ref = oracle_adjoint(*xm, *lm, grids[m])
+        for f in range(3):
+            got = g[f][m].to(torch.float64).cpu().numpy()
+            err = np.max(np.abs(got - ref[f])) / np.max(np.abs(ref[f]))
+            assert err <= 5e-6, (m, f, err)
