@@ -40,7 +40,7 @@ FLOP_PER_POINT = 53           # the paper's count for su, sv, sw (Sec. 2.3)
 BYTES_PER_POINT = {"f64": 48, "f32": 24, "f16s": 12}       # 3 fields in + 3 out
 ADJ_BYTES_PER_POINT = {"f64": 72, "f32": 36}                # 6 in + 3 out
 ADJ_SHAPE = (1024, 1024, 128)
-FP64_DFMA_PER_CLK_PER_SM = 2   # see the design doc (measured throughput probe)
+FP64_DFMA_PER_CLK_PER_SM = 2   # GB300 nominal (1.25 TFLOP/s FP64); a DFMA throughput probe reached 1.01
 N_SM = 152
 
 
@@ -352,7 +352,7 @@ def run_e2e(args, torch, op, winds, world, n_pts):
     for _ in range(e2e_steps):
         op.forward_host(*h_in, h_out)
     e2e_secs = (time.perf_counter() - t0) / e2e_steps
-    link = 343.0  # GB/s, concurrent pinned H2D + D2H measured on this machine's GB300
+    link = 343.0  # GB/s, concurrent pinned H2D + D2H copy rate measured on a GB300 (Grace C2C link)
     return {"value": world * n_pts / e2e_secs, "unit": UNIT,
             "h2d_bytes_per_step": 3 * n_pts * 8, "d2h_bytes_per_step": 3 * n_pts * 8,
             "ms_per_step": 1e3 * e2e_secs,
