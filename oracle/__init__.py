@@ -16,6 +16,10 @@ Parity status of each function (what pins it; the pins live in ``tests/``):
   arithmetic, impulse responses, zero tendency, reflection antisymmetry,
   periodic shift equivariance, power-of-two scaling, the su/sv transpose
   symmetry and discrete kinetic-energy conservation.
+* ``integrate``      -- exact agreement with the rational skew-symmetric
+  tendencies added to the base fields, the zero-step identity, and the
+  forward-Euler energy budget E(u + dt S) - E(u) = dt^2 <S, S> that the
+  scheme's energy conservation implies.
 * ``adjoint``        -- exact dot-product identity against the forward's
   tangent ``F(x+d) - F(x) - F(d)`` and exact central differences (the map is
   quadratic), both on dyadic inputs where FP64 is exact.
@@ -167,3 +171,19 @@ def adjoint(u, v, w, dsu, dsv, dsw, c: Coefficients):
     if rc != 0:
         raise ValueError("oracle_adjoint: invalid arguments")
     return tuple(outs)
+
+
+def integrate(u, v, w, c: Coefficients, dt, base=None):
+    """The source terms integrated into the flow fields (Sec. 2.1: later in
+    the timestep the source terms are added to the prognostic fields):
+    out_f = base_f + dt * s_f for f in u, v, w, with (su, sv, sw) from
+    ``forward`` and base = (u, v, w) unless given (one explicit step; a
+    leapfrog step passes the previous time level as base and 2 dt).  Returns
+    (u_out, v_out, w_out)."""
+    su, sv, sw = forward(u, v, w, c)
+    if base is None:
+        base = (u, v, w)
+    b = [_f64(x) for x in base]
+    _check_fields(su, *b)
+    dt = float(dt)
+    return tuple(bf + dt * s for bf, s in zip(b, (su, sv, sw)))

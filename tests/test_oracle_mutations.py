@@ -92,3 +92,45 @@ def test_pins_catch_planted_mistake(mutation, source, tmp_path):
         oracle.build = real_build
         oracle._lib_handle = saved
     assert caught, f"no pin caught mutation {mutation}"
+
+
+# Mistakes planted into the (Python) integration step of the oracle.
+INTEGRATE_MUTATIONS = {
+    "integrate_sign_flip": ("bf + dt * s for bf", "bf - dt * s for bf"),
+    "integrate_step_dropped": ("bf + dt * s for bf", "bf + s for bf"),
+    "integrate_half_step": ("bf + dt * s for bf", "bf + 0.5 * dt * s for bf"),
+    "integrate_ignores_base": ("base = (u, v, w)\n    b = [_f64(x) for x in base]",
+                               "base = (u, v, w)\n    b = [_f64(x) for x in (u, v, w)]"),
+    "integrate_fields_rotated": ("zip(b, (su, sv, sw))", "zip(b, (sv, sw, su))"),
+}
+
+
+@pytest.mark.parametrize("mutation", sorted(INTEGRATE_MUTATIONS))
+def test_integrate_pins_catch_planted_mistake(mutation):
+    import test_oracle_integrate_pins as int_pins
+    old, new = INTEGRATE_MUTATIONS[mutation]
+    src = inspect.getsource(oracle.integrate)
+    assert src.count(old) == 1, f"mutation anchor not unique: {mutation}"
+    ns = dict(vars(oracle))
+    exec(compile(src.replace(old, new), "<mutant>", "exec"), ns)
+    real = oracle.integrate
+    oracle.integrate = ns["integrate"]
+    caught = []
+    try:
+        for name, fn in inspect.getmembers(int_pins, inspect.isfunction):
+            if not name.startswith("test_"):
+                continue
+            params = [m for m in getattr(fn, "pytestmark", []) if m.name == "parametrize"]
+            cases = [{}]
+            if params:
+                argnames = [a.strip() for a in params[0].args[0].split(",")]
+                cases = [dict(zip(argnames, vals if isinstance(vals, tuple) else (vals,)))
+                         for vals in params[0].args[1]]
+            for kw in cases:
+                try:
+                    fn(**kw)
+                except (AssertionError, pytest.fail.Exception):
+                    caught.append(name)
+    finally:
+        oracle.integrate = real
+    assert caught, f"no pin caught mutation {mutation}"
