@@ -132,6 +132,33 @@ advect_status advect_forward(advect_ctx *ctx, const void *u, const void *v, cons
                              advect_stream stream);
 
 /*
+ * Forward pass fused with the step that integrates the source terms into the
+ * flow fields (Sec. 2.1: later in the timestep the source terms are added to
+ * the prognostic fields; the paper does not fix the time scheme):
+ *   u_out = u_base + dt * su(u,v,w),  v_out = v_base + dt * sv,  w_out = w_base + dt * sw
+ * at every point (so out = base on the levels where the source term is zero).
+ * u_base, v_base, w_base: all NULL for the winds themselves (one explicit
+ * step), or all three given (e.g. the previous time level with 2 dt for a
+ * leapfrog step).  The source terms are never written to memory: the kernel
+ * reads the three winds and writes the three results (plus reads the bases
+ * when given).  Same layout, element type and tile configuration as
+ * advect_forward; never runs the tuner.  In place: each base may be its own
+ * output (u_out == u_base), since every base element is read only by the
+ * thread that then writes that output element; a base must not otherwise
+ * overlap an output, and the outputs must not overlap u, v, w or each other
+ * (EINVAL).  dt must be finite (EINVAL).  scales (ADVECT_F16S only): 6 floats
+ * (u, v, w, then u_out, v_out, w_out) without bases, 9 with them (then
+ * u_base, v_base, w_base).  ADVECT_F64_FF: the base passes through the
+ * double-float type, so it is carried to a 47-bit significand (relative
+ * 2^-47) rather than returned bit for bit where the source term is zero.
+ * Asynchronous on stream.
+ */
+advect_status advect_forward_integrate(advect_ctx *ctx, const void *u, const void *v, const void *w,
+                                       const void *u_base, const void *v_base, const void *w_base,
+                                       double dt, void *u_out, void *v_out, void *w_out,
+                                       const float *scales, advect_stream stream);
+
+/*
  * Adjoint (vector-Jacobian product) of the forward pass with respect to all
  * of (u, v, w): (du, dv, dw) = J(u,v,w)^T (dsu, dsv, dsw).  Computed as a
  * gather (each output point sums the terms that read it; no atomics).

@@ -46,6 +46,7 @@ EXPORTS = (
     "advect_ensemble_create", "advect_ensemble_forward", "advect_ensemble_adjoint",
     "advect_sync", "advect_kernel_name", "advect_destroy", "advect_last_error",
     "advect_autotune", "advect_tuned_config", "advect_forward_noalloc",
+    "advect_forward_integrate",
 )
 
 NOALLOC_MAX_NZ = 512  # ADVECT_NOALLOC_MAX_NZ
@@ -74,6 +75,9 @@ def lib():
     L.advect_create.restype = st
     L.advect_forward.argtypes = [_vp] * 7 + [ctypes.POINTER(ctypes.c_float), _vp]
     L.advect_forward.restype = st
+    L.advect_forward_integrate.argtypes = ([_vp] * 7 + [ctypes.c_double] + [_vp] * 3
+                                           + [ctypes.POINTER(ctypes.c_float), _vp])
+    L.advect_forward_integrate.restype = st
     L.advect_adjoint.argtypes = [_vp] * 10 + [_vp]
     L.advect_adjoint.restype = st
     L.advect_forward_host.argtypes = [_vp] * 7 + [ctypes.POINTER(ctypes.c_float)]
@@ -160,6 +164,12 @@ def _scales(scales):
 
 def advect_forward(ctx, u, v, w, su, sv, sw, scales=None, stream=0) -> None:
     _check(lib().advect_forward(ctx, u, v, w, su, sv, sw, _scales(scales), stream))
+
+
+def advect_forward_integrate(ctx, u, v, w, u_base, v_base, w_base, dt, u_out, v_out, w_out,
+                             scales=None, stream=0) -> None:
+    _check(lib().advect_forward_integrate(ctx, u, v, w, u_base, v_base, w_base, float(dt),
+                                          u_out, v_out, w_out, _scales(scales), stream))
 
 
 def advect_adjoint(ctx, u, v, w, dsu, dsv, dsw, du, dv, dw, stream=0) -> None:

@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(OCC == 1 ? 256 : 128, OCC) adj_sweep_kernel(Ad
   for (int q = 0; q < 3; ++q) {
     t.sc.in[q] = 1.f;
     t.sc.inv_out[q] = 1.f;
+    t.sc.base[q] = 1.f;
   }
   t.f64_levels = 0;
   t.wait_budget = p.a.wait_budget;

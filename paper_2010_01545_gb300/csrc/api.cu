@@ -177,19 +177,28 @@ Coeffs coeffs_of(const Member& m) {
 
 namespace {
 
-advect_status read_scales(advect_ctx* ctx, const float* scales, Scales& sc) {
+advect_status read_scales(advect_ctx* ctx, const float* scales, Scales& sc, bool with_base = false) {
   for (int q = 0; q < 3; ++q) {
     sc.in[q] = 1.f;
     sc.inv_out[q] = 1.f;
+    sc.base[q] = 1.f;
   }
   if (ctx->dtype != ADVECT_F16S) return ADVECT_OK;
-  if (!scales) return fail(ADVECT_EINVAL, "F16S needs 6 scales (u, v, w, su, sv, sw)");
+  if (!scales)
+    return fail(ADVECT_EINVAL, with_base ? "F16S needs 9 scales (u, v, w, 3 outputs, 3 bases)"
+                                         : "F16S needs 6 scales (u, v, w, su, sv, sw)");
   for (int q = 0; q < 6; ++q)
     if (!(scales[q] > 0.f) || !std::isfinite(scales[q]))
       return fail(ADVECT_EINVAL, "scale %d must be positive and finite", q);
   for (int q = 0; q < 3; ++q) {
     sc.in[q] = scales[q];
     sc.inv_out[q] = 1.f / scales[3 + q];
+  }
+  if (with_base) {
+    for (int q = 6; q < 9; ++q)
+      if (!(scales[q] > 0.f) || !std::isfinite(scales[q]))
+        return fail(ADVECT_EINVAL, "scale %d must be positive and finite", q);
+    for (int q = 0; q < 3; ++q) sc.base[q] = scales[6 + q];
   }
   return ADVECT_OK;
 }
@@ -199,7 +208,7 @@ advect_status read_scales(advect_ctx* ctx, const float* scales, Scales& sc) {
 // Launch the forward on planes [i0, i1) of a single-grid context.
 advect_status advect_ctx::launch_forward(const void* u, const void* v, const void* w, void* su,
                                           void* sv, void* sw, const Scales& sc, int i0, int i1,
-                                          cudaStream_t st) {
+                                          cudaStream_t st, const Step* step) {
   const Member& m = members[0];
   FwdArgs a;
   a.u = u; a.v = v; a.w = w;
@@ -212,7 +221,15 @@ advect_status advect_ctx::launch_forward(const void* u, const void* v, const voi
   a.i1 = i1;
   a.wait_budget = wait_budget;
   a.skip_plane = test_skip_plane;
-  if (tune_fwd) {
+  if (step) {
+    a.integ = 1;
+    a.bu = step->b[0];
+    a.bv = step->b[1];
+    a.bw = step->b[2];
+    a.dt = step->dt;
+    a.dt_hi = (float)step->dt;
+    a.dt_lo = (float)(step->dt - (double)a.dt_hi);
+  } else if (tune_fwd) {
     tune_fwd = false;
     cudaError_t e = tune_single(*this, 0, &a, nullptr, st);
     if (e != cudaSuccess) return cuda_fail(e, "forward tuning");
@@ -309,6 +326,44 @@ advect_status advect_forward(advect_ctx* ctx, const void* u, const void* v, cons
   s = read_scales(ctx, scales, sc);
   if (s) return s;
   return ctx->launch_forward(u, v, w, su, sv, sw, sc, 0, m.nx, (cudaStream_t)stream);
+}
+
+advect_status advect_forward_integrate(advect_ctx* ctx, const void* u, const void* v, const void* w,
+                                       const void* u_base, const void* v_base, const void* w_base, double dt,
+                                       void* u_out, void* v_out, void* w_out, const float* scales,
+                                       advect_stream stream) {
+  if (!ctx) return fail(ADVECT_EINVAL, "context is NULL");
+  if (ctx->ensemble) return fail(ADVECT_EINVAL, "ensemble context: the integration step is single-grid only");
+  if (!is_finite(dt)) return fail(ADVECT_EINVAL, "dt must be finite");
+  const int nb = (u_base != nullptr) + (v_base != nullptr) + (w_base != nullptr);
+  if (nb != 0 && nb != 3) return fail(ADVECT_EINVAL, "give all three base fields or none");
+  const Member& m = ctx->members[0];
+  const size_t elem = elem_bytes(ctx->dtype);
+  const size_t bytes = (size_t)m.nx * m.ny * m.nz * elem;
+  const void* in[3] = {u, v, w};
+  void* outp[3] = {u_out, v_out, w_out};
+  static const char* names[6] = {"u", "v", "w", "u_out", "v_out", "w_out"};
+  advect_status s = check_buffers(in, 3, outp, 3, names, bytes, elem, ctx->device);
+  if (s) return s;
+  const void* base[3] = {u_base, v_base, w_base};
+  static const char* bnames[3] = {"u_base", "v_base", "w_base"};
+  if (nb == 3) {
+    for (int f = 0; f < 3; ++f) {
+      s = check_device_ptr(base[f], bnames[f], elem, ctx->device);
+      if (s) return s;
+      // each base element is read by the thread that then writes that output
+      // element, so a base may be its own output (in place), but must not
+      // overlap any other output
+      for (int o = 0; o < 3; ++o)
+        if (!(o == f && base[f] == outp[o]) && overlaps(base[f], outp[o], bytes))
+          return fail(ADVECT_EINVAL, "base %s overlaps output %s", bnames[f], names[3 + o]);
+    }
+  }
+  Scales sc;
+  s = read_scales(ctx, scales, sc, nb == 3);
+  if (s) return s;
+  const advect_ctx::Step step{{base[0], base[1], base[2]}, dt};
+  return ctx->launch_forward(u, v, w, u_out, v_out, w_out, sc, 0, m.nx, (cudaStream_t)stream, &step);
 }
 
 advect_status advect_adjoint(advect_ctx* ctx, const void* u, const void* v, const void* w,

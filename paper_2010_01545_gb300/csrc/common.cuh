@@ -34,7 +34,8 @@ struct Shape {
 // Scales for F16S (stored = true / scale); unused for other types.
 struct Scales {
   float in[3];       // u, v, w
-  float inv_out[3];  // 1 / scale of su, sv, sw
+  float inv_out[3];  // 1 / scale of su, sv, sw (or of the integrated fields)
+  float base[3];     // base fields of an integration step
 };
 
 template <typename T>

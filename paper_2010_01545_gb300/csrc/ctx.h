@@ -55,8 +55,16 @@ struct advect_ctx {
   long long wait_budget = 2LL * 1000 * 1000 * 1000;
   std::string cfg_text[2];                  // storage for advect_tuned_config
 
+  // step != NULL: the integration epilogue (base fields step->b, NULL for
+  // the winds, and step->dt); such calls never run the tuner, because an
+  // in-place step must not be applied more than once.
+  struct Step {
+    const void* b[3];
+    double dt;
+  };
   advect_status launch_forward(const void* u, const void* v, const void* w, void* su, void* sv,
-                               void* sw, const advect::Scales& sc, int i0, int i1, cudaStream_t st);
+                               void* sw, const advect::Scales& sc, int i0, int i1, cudaStream_t st,
+                               const Step* step = nullptr);
   advect_status ensure_host_path(size_t bytes);
   void release();
 };

@@ -269,7 +269,7 @@ void select_kernels(advect_ctx& ctx) {
 
 cudaError_t launch_fwd(const advect_ctx& ctx, const FwdArgs& a, cudaStream_t st) {
   if (ctx.fwd_kind == 1 && aligned16(a.u) && aligned16(a.v) && aligned16(a.w) && aligned16(a.su) &&
-      aligned16(a.sv) && aligned16(a.sw))
+      aligned16(a.sv) && aligned16(a.sw) && aligned16(a.bu) && aligned16(a.bv) && aligned16(a.bw))
     return launch_fwd_sweep((int)ctx.dtype, a, ctx.sweep, ctx.d_flag, st);
   return launch_fwd_point((int)ctx.dtype, a, st);
 }

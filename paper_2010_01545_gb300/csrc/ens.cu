@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(kEnsThreads, OCC) ens_kernel(EnsParams p) {
     for (int q = 0; q < 3; ++q) {
       t.sc.in[q] = 1.f;
       t.sc.inv_out[q] = 1.f;
+      t.sc.base[q] = 1.f;
     }
     t.f64_levels = 0;
     const bool ok = ADJ ? sweep::adjoint_tile<T, SPLIT>(t, R, p.flag)

@@ -41,6 +41,13 @@ __global__ void __launch_bounds__(OCC == 1 ? 256 : 128, OCC) fwd_sweep_kernel(Sw
   t.f64_levels = p.a.f64_levels;
   t.wait_budget = p.a.wait_budget;
   t.skip_plane = p.a.skip_plane;
+  t.integ = p.a.integ;
+  t.b[0] = (const T*)p.a.bu;
+  t.b[1] = (const T*)p.a.bv;
+  t.b[2] = (const T*)p.a.bw;
+  t.dt = p.a.dt;
+  t.dt_hi = p.a.dt_hi;
+  t.dt_lo = p.a.dt_lo;
   sweep::forward_tile<T, F64Z, SPLIT>(t, R, p.flag);
 }
 

@@ -20,6 +20,13 @@ struct FwdArgs {
   int i0, i1;      // x-planes [i0, i1) are computed (the others are untouched)
   long long wait_budget = 2LL * 1000 * 1000 * 1000;  // clock64 cycles per bounded wait
   int skip_plane = -1;  // test-only: plane index of each tile whose copy is never issued
+  // Integration epilogue: when integ != 0 the outputs are base + dt * (su, sv,
+  // sw) instead of the source terms; base = (bu, bv, bw), or the winds
+  // themselves where bu is NULL.  dt_hi + dt_lo is dt split into binary32.
+  int integ = 0;
+  const void *bu = nullptr, *bv = nullptr, *bw = nullptr;
+  double dt = 0.0;
+  float dt_hi = 0.f, dt_lo = 0.f;
 };
 
 struct AdjArgs {

@@ -97,6 +97,7 @@ extern "C" advect_status advect_forward_noalloc(int nx, int ny, int nz, const ad
   for (int q = 0; q < 3; ++q) {
     sc.in[q] = 1.f;
     sc.inv_out[q] = 1.f;
+    sc.base[q] = 1.f;
   }
   if (dtype == ADVECT_F16S) {
     if (!scales) return fail(ADVECT_EINVAL, "F16S needs 6 scales (u, v, w, su, sv, sw)");

@@ -24,6 +24,11 @@ struct Grid3 {
   }
 };
 
+// The integration step dt in each arithmetic type.
+__device__ __forceinline__ void step_into(double& o, const FwdArgs& a) { o = a.dt; }
+__device__ __forceinline__ void step_into(float& o, const FwdArgs& a) { o = a.dt_hi; }
+__device__ __forceinline__ void step_into(ff& o, const FwdArgs& a) { o = ff(a.dt_hi, a.dt_lo); }
+
 // ---------------------------------------------------------------- forward
 // su, sv, sw at one point: Listing 1 (Sec. 2.1) for su and the same pattern
 // for sv (x<->y) and sw (w cell).  The top-level branch of Listing 1 comes
@@ -92,6 +97,16 @@ fwd_point_kernel(FwdArgs a) {
         ow = ow + d1 * wzm * (w0 + wzm) - d2 * wzp * (w0 + wzp);
       }
       if (k == nz - 1) ow = 0;
+    }
+    if (a.integ) {  // integration epilogue: base + dt * source term
+      C dt;
+      step_into(dt, a);
+      const C bu = a.bu ? S::load((const T*)a.bu, t, a.sc.base[0]) : U.at(i, j, k);
+      const C bv = a.bv ? S::load((const T*)a.bv, t, a.sc.base[1]) : V.at(i, j, k);
+      const C bw = a.bw ? S::load((const T*)a.bw, t, a.sc.base[2]) : W.at(i, j, k);
+      ou = bu + dt * ou;
+      ov = bv + dt * ov;
+      ow = bw + dt * ow;
     }
     S::store(su, t, ou, a.sc.inv_out[0]);
     S::store(sv, t, ov, a.sc.inv_out[1]);

@@ -41,6 +41,11 @@ struct VecIO<double> {
     o[1] = x.y;
   }
   __device__ static __forceinline__ C ld1(const double* s, float) { return *s; }
+  __device__ static __forceinline__ void gld(const double* g, float, C (&o)[P]) {
+    const double2 x = __ldcs(reinterpret_cast<const double2*>(g));
+    o[0] = x.x;
+    o[1] = x.y;
+  }
   __device__ static __forceinline__ void st(double* g, const C (&v)[P], float) {
     __stcs(reinterpret_cast<double2*>(g), make_double2(v[0], v[1]));
   }
@@ -58,6 +63,13 @@ struct VecIO<float> {
     o[3] = x.w;
   }
   __device__ static __forceinline__ C ld1(const float* s, float) { return *s; }
+  __device__ static __forceinline__ void gld(const float* g, float, C (&o)[P]) {
+    const float4 x = __ldcs(reinterpret_cast<const float4*>(g));
+    o[0] = x.x;
+    o[1] = x.y;
+    o[2] = x.z;
+    o[3] = x.w;
+  }
   __device__ static __forceinline__ void st(float* g, const C (&v)[P], float) {
     __stcs(reinterpret_cast<float4*>(g), make_float4(v[0], v[1], v[2], v[3]));
   }
@@ -77,6 +89,15 @@ struct VecIO<__half> {
     o[3] = b.y * sc;
   }
   __device__ static __forceinline__ C ld1(const __half* s, float sc) { return __half2float(*s) * sc; }
+  __device__ static __forceinline__ void gld(const __half* g, float sc, C (&o)[P]) {
+    const uint2 x = __ldcs(reinterpret_cast<const uint2*>(g));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&x.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&x.y));
+    o[0] = a.x * sc;
+    o[1] = a.y * sc;
+    o[2] = b.x * sc;
+    o[3] = b.y * sc;
+  }
   __device__ static __forceinline__ void st(__half* g, const C (&v)[P], float inv) {
     const __half2 a = __floats2half2_rn(v[0] * inv, v[1] * inv);
     const __half2 b = __floats2half2_rn(v[2] * inv, v[3] * inv);
@@ -97,10 +118,20 @@ struct VecIO<f64ff> {
     o[1] = ff(x.y);
   }
   __device__ static __forceinline__ C ld1(const f64ff* s, float) { return ff(s->v); }
+  __device__ static __forceinline__ void gld(const f64ff* g, float, C (&o)[P]) {
+    const double2 x = __ldcs(reinterpret_cast<const double2*>(g));
+    o[0] = ff(x.x);
+    o[1] = ff(x.y);
+  }
   __device__ static __forceinline__ void st(f64ff* g, const C (&v)[P], float) {
     __stcs(reinterpret_cast<double2*>(g), make_double2((double)v[0], (double)v[1]));
   }
 };
+
+// The integration step dt in each arithmetic type.
+__device__ __forceinline__ double step_of(double, double dt, float, float) { return dt; }
+__device__ __forceinline__ float step_of(float, double, float hi, float) { return hi; }
+__device__ __forceinline__ ff step_of(const ff&, double, float hi, float lo) { return ff(hi, lo); }
 
 // Warp shuffles for every arithmetic type.
 __device__ __forceinline__ float shfl_up_c(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
@@ -150,7 +181,30 @@ struct Tile {
   int f64_levels;
   long long wait_budget = kWaitBudgetCycles;  // clock64 cycles per bounded wait
   int skip_plane = -1;  // test-only fault injection: this plane's copy is never issued
+  // Integration epilogue (forward only): outputs base + dt * source term,
+  // base = b[f], or the winds where b[0] is NULL.
+  int integ = 0;
+  const T* b[3] = {nullptr, nullptr, nullptr};
+  double dt = 0.0;
+  float dt_hi = 0.f, dt_lo = 0.f;
 };
+
+// Integration epilogue of one field: s = base + dt * s, the base read with a
+// streaming global load (each element by the one thread that overwrites the
+// output there, so the output may be the base itself) or taken from x, the
+// thread's own wind values.
+template <typename T, typename C, int P>
+__device__ __forceinline__ void add_step(const T* base, size_t o, float scale, const C (&x)[P], C dt, C (&s)[P]) {
+  C b[P];
+  if (base) {
+    VecIO<T>::gld(base + o, scale, b);
+  } else {
+#pragma unroll
+    for (int q = 0; q < P; ++q) b[q] = x[q];
+  }
+#pragma unroll
+  for (int q = 0; q < P; ++q) s[q] = b[q] + dt * s[q];
+}
 
 // Bulk-copy plane ql of the tile (x index i_lo-1+ql, periodic) into its slot;
 // NF fields (t.nf == NF).
@@ -474,6 +528,12 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
       }
       if (row_ok) {
         const size_t o = ((size_t)i * ny + j) * nz + k0;
+        if (t.integ) {
+          const C dt = step_of(C(0), t.dt, t.dt_hi, t.dt_lo);
+          add_step<T, C, P>(t.b[0], o, t.sc.base[0], U0, dt, ou);
+          add_step<T, C, P>(t.b[1], o, t.sc.base[1], V0, dt, ov);
+          add_step<T, C, P>(t.b[2], o, t.sc.base[2], W0, dt, ow);
+        }
         IO::st(t.o[0] + o, ou, t.sc.inv_out[0]);
         IO::st(t.o[1] + o, ov, t.sc.inv_out[1]);
         IO::st(t.o[2] + o, ow, t.sc.inv_out[2]);

@@ -76,6 +76,19 @@ class Advect:
                             sv.data_ptr(), sw.data_ptr(), scales, _stream())
         return su, sv, sw
 
+    def integrate(self, u, v, w, dt, base=None, out=None, scales=None):
+        """(base + dt * su, base + dt * sv, base + dt * sw) in one kernel; base
+        defaults to (u, v, w).  out may be base itself (in-place step)."""
+        self._check(u, v, w)
+        if base is not None:
+            self._check(*base)
+        uo, vo, wo = out if out is not None else (self.empty(), self.empty(), self.empty())
+        self._check(uo, vo, wo)
+        bp = [b.data_ptr() for b in base] if base is not None else [None] * 3
+        _abi.advect_forward_integrate(self.handle, u.data_ptr(), v.data_ptr(), w.data_ptr(), *bp, dt,
+                                      uo.data_ptr(), vo.data_ptr(), wo.data_ptr(), scales, _stream())
+        return uo, vo, wo
+
     def adjoint(self, u, v, w, dsu, dsv, dsw, out=None):
         self._check(u, v, w, dsu, dsv, dsw)
         du, dv, dw = out if out is not None else (self.empty(), self.empty(), self.empty())

@@ -107,6 +107,7 @@ def test_null_context_and_null_out_are_errors(lib):
     assert L.advect_forward(None, None, None, None, None, None, None, None, None) == 1
     assert "NULL" in _abi.advect_last_error()
     assert L.advect_adjoint(*([None] * 11)) == 1
+    assert L.advect_forward_integrate(*([None] * 7), 0.5, *([None] * 5)) == 1
     assert L.advect_sync(None, None) == 1
     assert L.advect_create(4, 4, 8, None, 0, None) == 1
     L.advect_destroy(None)          # NULL-safe

@@ -65,6 +65,27 @@ def test_forward_f32_2048x2048x64_sampled(big_winds):
     torch.cuda.empty_cache()
 
 
+def test_integrate_f64_2048x2048x64_in_place_sampled(big_winds):
+    """The fused step, in place on a separate base, at the benchmark size."""
+    shape = (2048, 2048, 64)
+    op, grid = make_op(shape, "f64")
+    base = workload.winds(*shape, seed=workload.DEFAULT_SEED + 7)
+    dt = 0.37
+    x = [dev(a) for a in big_winds]
+    b = [dev(a) for a in base]
+    out = op.integrate(*x, dt, base=b, out=b)
+    torch.cuda.synchronize()
+    idx = sample_indices(shape, 20000, 3)
+    s = oracle.forward_points(*big_winds, oracle.coefficients(grid), idx)
+    for f in range(3):
+        g = out[f].reshape(-1)[torch.from_numpy(idx).cuda()].cpu().numpy()
+        r = base[f].reshape(-1)[idx] + dt * s[:, f]
+        bound = 1e-12 * dt * np.max(np.abs(s[:, f])) + 2.0 ** -51 * np.max(np.abs(r))
+        assert np.max(np.abs(g - r)) <= bound, f"field {f}"
+    del x, b, out
+    torch.cuda.empty_cache()
+
+
 def test_adjoint_f64_1024x1024x128_dot_product_and_probes():
     shape = (1024, 1024, 128)
     op, _ = make_op(shape, "f64")
