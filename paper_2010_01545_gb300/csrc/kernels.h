@@ -55,6 +55,9 @@ cudaError_t launch_adj_point(int dtype, const AdjArgs& a, cudaStream_t st);
 int sweep_vec(int elem);
 size_t sweep_smem_bytes(int nz, int elem, const SweepCfg& cfg);
 cudaError_t launch_fwd_sweep(int dtype, const FwdArgs& a, const SweepCfg& cfg, int* flag, cudaStream_t st);
+// The same sweep with the integration epilogue (a.integ != 0; fwd_integ.cu).
+cudaError_t launch_fwd_sweep_integ(int dtype, const FwdArgs& a, const SweepCfg& cfg, int* flag,
+                                   cudaStream_t st);
 
 // Adjoint plane sweep (F64, F32): nz % adj_sweep_vec(elem) == 0, nz * elem % 16
 // == 0, 16-byte aligned fields, ty * nz / adj_sweep_vec(elem) a multiple of 32.

@@ -181,8 +181,8 @@ struct Tile {
   int f64_levels;
   long long wait_budget = kWaitBudgetCycles;  // clock64 cycles per bounded wait
   int skip_plane = -1;  // test-only fault injection: this plane's copy is never issued
-  // Integration epilogue (forward only): outputs base + dt * source term,
-  // base = b[f], or the winds where b[0] is NULL.
+  // Integration epilogue (forward_tile<..., INTEG = true> only): outputs
+  // base + dt * source term, base = b[f], or the winds where b[f] is NULL.
   int integ = 0;
   const T* b[3] = {nullptr, nullptr, nullptr};
   double dt = 0.0;
@@ -339,7 +339,9 @@ __device__ __forceinline__ C halo_above(const C (&a)[P], const T* row, int k0, i
 // bounded budget.  Returns false if any wait of this thread's warp timed out.
 // F64Z: compile the binary64 near-surface branch (F32/F16S with
 // f64_levels > 0); the default instantiation has no binary64 code at all.
-template <typename T, bool F64Z = false, bool SPLIT = true>
+// INTEG: compile the integration epilogue (t.integ must then be set); the
+// plain forward has none of its code.
+template <typename T, bool F64Z = false, bool SPLIT = true, bool INTEG = false>
 __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
   using IO = VecIO<T>;
   using C = typename IO::C;
@@ -528,7 +530,7 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
       }
       if (row_ok) {
         const size_t o = ((size_t)i * ny + j) * nz + k0;
-        if (t.integ) {
+        if constexpr (INTEG) {
           const C dt = step_of(C(0), t.dt, t.dt_hi, t.dt_lo);
           add_step<T, C, P>(t.b[0], o, t.sc.base[0], U0, dt, ou);
           add_step<T, C, P>(t.b[1], o, t.sc.base[1], V0, dt, ov);
