@@ -16,10 +16,11 @@
 // about 1e-14 (the tests bound it by 1e-12).
 //
 // Conversions never touch the binary64 pipe: splitting a double into (hi, lo)
-// and assembling (hi, lo) into the nearest-below double are integer bit
-// operations plus binary32 arithmetic.  Range: magnitudes in [2^-80, 2^126];
-// smaller inputs lose relative precision (the low part underflows), zero is
-// exact, and non-finite inputs are not supported.
+// and assembling (hi, lo) into the truncated double are a dozen integer bit
+// operations plus one binary32 subtraction or renormalisation each.  Range:
+// magnitudes in [2^-80, 2^126]; smaller inputs lose relative precision (the
+// low part underflows), zero is exact, and non-finite inputs are not
+// supported.
 #pragma once
 
 #include <stdint.h>
@@ -67,41 +68,45 @@ __device__ __forceinline__ ff& operator-=(ff& x, const ff& y) { return x = x - y
 
 // double -> (hi, lo): hi is x with its significand truncated to 24 bits
 // (exact in binary32); lo holds the next 23 bits of the remainder.
+//   hi: the top word with its exponent rebiased from 1023 to 127, funnel-
+//       shifted left by 3 to take the first 3 bits of the low word, sign
+//       put back;
+//   lo: the 23 remainder bits placed under the exponent of 2^(e-23) minus
+//       2^(e-23) itself -- an exact binary32 subtraction giving rem*2^(e-46).
+// Zero and magnitudes below 2^-104 give (+-0, 0); below 2^-80 lo may be
+// subnormal (and is dropped by the assembly below).
 __device__ __forceinline__ ff::ff(double x) {
   const uint64_t b = (uint64_t)__double_as_longlong(x);
   const uint32_t top = (uint32_t)(b >> 32), bot = (uint32_t)b;
   const uint32_t sign = top & 0x80000000u;
-  const int e = (int)((top >> 20) & 0x7ff) - 1023;  // unbiased exponent
-  const uint32_t hib = sign | ((uint32_t)(e + 127) << 23) | ((top & 0xfffffu) << 3) | (bot >> 29);
-  // remainder: the low 29 significand bits, scaled 2^(e-52); keep the top 23
-  const uint32_t rem = (bot & 0x1fffffffu) >> 6;
-  const float r = __uint_as_float(0x4b000000u | rem) - 8388608.0f;  // exact integer rem
-  const int se = e - 46 + 127;                                    // 2^(e-46)
-  const float scale = __uint_as_float((uint32_t)max(se, 1) << 23);
-  const float l = __uint_as_float(__float_as_uint(r * scale) | sign);
-  const bool tiny = e < -126;  // zero or below the binary32 normal range
-  hi = tiny ? __uint_as_float(sign) : __uint_as_float(hib);
-  lo = (tiny || se < 1) ? 0.f : l;
+  const uint32_t mag = __funnelshift_l(bot, top - 0x38000000u, 3) & 0x7fffffffu;
+  const uint32_t base = (mag & 0x7f800000u) - 0x0b800000u;  // 2^(e-23)
+  const uint32_t rem = (bot >> 6) & 0x7fffffu;
+  const float l = __uint_as_float(base | rem) - __uint_as_float(base);
+  const bool tiny = (top & 0x7fffffffu) < 0x39700000u;
+  hi = __uint_as_float(tiny ? sign : (mag | sign));
+  lo = tiny ? 0.f : __uint_as_float(__float_as_uint(l) | sign);
 }
 
 // (hi, lo) -> double: renormalise, then add lo into hi's binary64 pattern as
-// an integer multiple of hi's binary64 ulp (truncated).
+// an integer multiple of hi's binary64 ulp (truncated).  After the
+// renormalisation |lo| <= ulp32(hi)/2, so that multiple fits in 29 bits.
 __device__ __forceinline__ ff::operator double() const {
   // |hi| >= |lo| is not guaranteed after unnormalised arithmetic: order them
   const ff n = fabsf(hi) >= fabsf(lo) ? fast_two_sum(hi, lo) : fast_two_sum(lo, hi);
   const uint32_t hb = __float_as_uint(n.hi), lb = __float_as_uint(n.lo);
-  const uint32_t eh = (hb >> 23) & 0xffu;
-  const uint32_t mh = hb & 0x7fffffu;
-  const uint64_t d = ((uint64_t)(hb & 0x80000000u) << 32) | ((uint64_t)(eh + 896u) << 52) | ((uint64_t)mh << 29);
-  const uint32_t el = (lb >> 23) & 0xffu;
+  const uint32_t mag = hb & 0x7fffffffu;
+  const uint32_t dh = ((mag >> 3) + 0x38000000u) | (hb & 0x80000000u);  // exponent 127 -> 1023
+  const uint32_t dl = hb << 29;
+  const int sh = (int)((lb >> 23) & 0xffu) - (int)(mag >> 23) + 29;  // lo / ulp64(hi) = ml * 2^sh
   const uint32_t ml = (lb & 0x7fffffu) | 0x800000u;
-  const int sh = (int)el - (int)eh + 29;  // lo = ml * 2^(el-127-23), ulp(d) = 2^(eh-127-52)
-  uint64_t L = sh >= 0 ? ((uint64_t)ml << min(sh, 31)) : (uint64_t)(ml >> min(-sh, 31));
-  L = el == 0 ? 0ull : L;  // lo zero (or below the binary32 normal range)
+  uint32_t L = sh >= 0 ? ml << sh : __funnelshift_rc(ml, 0u, (uint32_t)(-sh));
+  L = (lb & 0x7f800000u) == 0 ? 0u : L;  // lo zero (or below the binary32 normal range)
   const bool opposite = ((hb ^ lb) & 0x80000000u) != 0;
-  L = (opposite && mh == 0) ? L << 1 : L;  // hi a power of two: the result lies in the binade below
-  const uint64_t r = opposite ? d - L : d + L;
-  return eh == 0 ? 0.0 : __longlong_as_double((long long)r);  // zero (binary32 subnormals as zero)
+  L = (opposite && (hb & 0x7fffffu) == 0) ? L << 1 : L;  // hi a power of two: the binade below
+  const long long sL = opposite ? -(long long)L : (long long)L;
+  const unsigned long long r = (((unsigned long long)dh << 32) | dl) + (unsigned long long)sL;
+  return (mag >> 23) == 0 ? 0.0 : __longlong_as_double((long long)r);  // zero (binary32 subnormals as zero)
 }
 
 __device__ __forceinline__ ff shfl_up(const ff& v, int d) {
