@@ -254,6 +254,8 @@ def main():
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "f16s", "f64ff"],
                     help="element type of the --shape case")
     ap.add_argument("--adjoint", action="store_true", help="--shape case runs the adjoint")
+    ap.add_argument("--integrate", action="store_true",
+                    help="--shape case runs the forward fused with the integration step")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -401,7 +403,9 @@ def measure_link(torch, h_in, h_out, reps=3):
 
 
 def run_case(args):
-    """A forward-only case of another shape / type, for profiling."""
+    """One kernel on another shape / type, for profiling: the forward, the
+    adjoint (--adjoint) or the forward fused with the integration step
+    (--integrate: a separate base updated in place, dt = 0.5)."""
     import torch
 
     import workload
@@ -423,12 +427,17 @@ def run_case(args):
     if args.adjoint:
         lam = [torch.from_numpy(a).to("cuda", op.torch_dtype) for a in workload.cotangents(*shape)]
         call = lambda: op.adjoint(*d, *lam, out=out)  # noqa: E731
+    elif args.integrate:
+        if args.dtype == "f16s":
+            raise SystemExit("--integrate takes f64, f32 or f64ff")
+        base = [t.clone() for t in d]
+        call = lambda: op.integrate(*d, 0.5, base=base, out=base)  # noqa: E731
     else:
         call = lambda: op.forward(*d, out=out, scales=scales)  # noqa: E731
     for _ in range(args.warmup):
         call()
     secs = time_calls(call, args.steps, torch.cuda.current_stream()) / args.steps
-    kind = "adj" if args.adjoint else "fwd"
+    kind = "adj" if args.adjoint else ("int" if args.integrate else "fwd")
     print(json.dumps({"case": f"{kind}_{args.dtype}_{shape[0]}x{shape[1]}x{shape[2]}",
                       "kernel": op.kernel_name(args.adjoint), "tile": op.tuned_config(args.adjoint),
                       "ms": 1e3 * secs, "points_per_s": n_pts / secs, "steps": args.steps,
