@@ -64,7 +64,7 @@ typedef enum {
     ADVECT_EINVAL = 1,        /* bad argument: sizes, NULL, alias, alignment */
     ADVECT_ENOMEM = 2,        /* host or device allocation failed            */
     ADVECT_ECUDA = 3,         /* a CUDA runtime call failed                  */
-    ADVECT_EUNSUPPORTED = 4,  /* valid request this build does not offer     */
+    ADVECT_EUNSUPPORTED = 4,  /* valid request the library does not offer  */
     ADVECT_ETIMEOUT = 5       /* a kernel gave up a bounded wait             */
 } advect_status;
 
