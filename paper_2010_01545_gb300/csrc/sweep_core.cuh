@@ -22,6 +22,8 @@
 // tzc2[nz-1] == 0 and zero values above the top level.
 #pragma once
 
+#include <type_traits>
+
 #include "bulk.cuh"
 #include "kernels.h"
 
@@ -362,7 +364,29 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
     const int k0 = kb * P;
     const int j = t.j0 + rr;
     const bool row_ok = j < ny;
-    const float s_u = t.sc.in[0], s_v = t.sc.in[1], s_w = t.sc.in[2];
+    // F16S: the input scales are powers of two, so they fold exactly into
+    // the constants.  With raw (unscaled) values every product is u*u, u*v,
+    // u*w, v*v, v*w or w*w scaled by the product of two field scales; taking
+    // tcx' = tcx s_u / s_w and tcy' = tcy s_v / s_w makes each field's sum
+    // the true one times 1 / (s_f s_w), which the output scale then absorbs.
+    // Same rounding as scaling every loaded value, one multiply fewer per
+    // value.  (Not with the binary64 near-surface terms or the integration
+    // epilogue, which need true values.)
+    constexpr bool kFold = std::is_same<T, __half>::value && !F64Z && !INTEG;
+    float s_u = t.sc.in[0], s_v = t.sc.in[1], s_w = t.sc.in[2];
+    float o_u = t.sc.inv_out[0], o_v = t.sc.inv_out[1], o_w = t.sc.inv_out[2];
+    C tcx = S::tcx(t.c), tcy = S::tcy(t.c);
+    if constexpr (kFold) {
+      const float iw = 1.f / s_w;
+      tcx = tcx * s_u * iw;
+      tcy = tcy * s_v * iw;
+      o_u = o_u * s_u * s_w;
+      o_v = o_v * s_v * s_w;
+      o_w = o_w * s_w * s_w;
+      s_u = 1.f;
+      s_v = 1.f;
+      s_w = 1.f;
+    }
     const int r = rr + 1;
     const int o_u0 = r * nz, o_um = (r - 1) * nz, o_up = (r + 1) * nz;
     const int o_v0 = (rows + r) * nz, o_vm = (rows + r - 1) * nz, o_vp = (rows + r + 1) * nz;
@@ -388,7 +412,6 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
       d1[q] = S::coef(t.c, TZD1, nz, k);
       d2[q] = S::coef(t.c, TZD2, nz, k);
     }
-    const C tcx = S::tcx(t.c), tcy = S::tcy(t.c);
 
     // Face sums shared with the previous plane: rolled in registers where the
     // arithmetic is the bottleneck (binary64, double-float); recomputed (three
@@ -536,9 +559,9 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
           add_step<T, C, P>(t.b[1], o, t.sc.base[1], V0, dt, ov);
           add_step<T, C, P>(t.b[2], o, t.sc.base[2], W0, dt, ow);
         }
-        IO::st(t.o[0] + o, ou, t.sc.inv_out[0]);
-        IO::st(t.o[1] + o, ov, t.sc.inv_out[1]);
-        IO::st(t.o[2] + o, ow, t.sc.inv_out[2]);
+        IO::st(t.o[0] + o, ou, o_u);
+        IO::st(t.o[1] + o, ov, o_v);
+        IO::st(t.o[2] + o, ow, o_w);
       }
       uxmp = u0p;
 #pragma unroll
