@@ -184,3 +184,38 @@ def test_integrate_validation():
     with pytest.raises(AdvectError):
         _abi.advect_forward_integrate(op16.handle, *p(h), None, None, None, 0.5,
                                       *p([torch.empty_like(h[0]) for _ in range(3)]), None)
+
+
+@pytest.mark.parametrize("f64_levels", [2, 64])
+def test_integrate_f32_with_binary64_near_surface_levels(f64_levels):
+    shape = (40, 24, 64)
+    op, grid = make_op(shape, "f32", f64_levels=f64_levels)
+    x, b = _inputs(shape, "f32", seed=58)
+    dt = 0.37
+    bd = [dev(a, torch.float32) for a in b]
+    out = op.integrate(*(dev(a, torch.float32) for a in x), dt, base=bd, out=bd)
+    ref = oracle.integrate(*x, oracle.coefficients(grid), dt, base=b)
+    _check([host(t) for t in out], ref, oracle_forward(*x, grid), dt, "f32", f"f64_levels={f64_levels}")
+
+
+def test_in_place_step_is_applied_once_with_tuning_armed(tmp_path, monkeypatch):
+    """The tuner times candidates by repeating a call; an in-place step must
+    never be repeated, so the integration call leaves tuning to the next
+    plain forward."""
+    monkeypatch.setenv("ADVECT_TUNE_CACHE", str(tmp_path / "tune.json"))
+    shape = (64, 48, 64)
+    op, grid = make_op(shape, "f32")
+    op.autotune(True)
+    x, b = _inputs(shape, "f32", seed=59)
+    dt = 0.5
+    xd = [dev(a, torch.float32) for a in x]
+    bd = [dev(a, torch.float32) for a in b]
+    op.integrate(*xd, dt, base=bd, out=bd)
+    ref = oracle.integrate(*x, oracle.coefficients(grid), dt, base=b)
+    s_ref = oracle_forward(*x, grid)
+    _check([host(t) for t in bd], ref, s_ref, dt, "f32", "in place with tuning armed")
+    # the next forward tunes and is still correct
+    su = op.forward(*xd)
+    for g, r in zip(su, s_ref):
+        assert np.max(np.abs(host(g) - r)) <= 2e-6 * np.max(np.abs(r))
+    assert (tmp_path / "tune.json").exists()
