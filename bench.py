@@ -363,13 +363,18 @@ def run_e2e(args, torch, op, winds, world, n_pts):
     e2e_steps = max(3, min(args.steps, 10))
     for _ in range(2):
         op.forward_host(*h_in, h_out)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         op.forward_host(*h_in, h_out)
-    e2e_secs = (time.perf_counter() - t0) / e2e_steps
+    # all ranks' points over the slowest rank's time
+    value, total = whole_job_rate(n_pts * e2e_steps, time.perf_counter() - t0, "cuda")
+    e2e_secs = total / e2e_steps
     link_secs = measure_link(torch, h_in, h_out)
     moved = 6 * n_pts * 8
-    return {"value": world * n_pts / e2e_secs, "unit": UNIT,
+    return {"value": value, "unit": UNIT,
             "h2d_bytes_per_step": 3 * n_pts * 8, "d2h_bytes_per_step": 3 * n_pts * 8,
             "ms_per_step": 1e3 * e2e_secs,
             "link_bound_ms": 1e3 * link_secs, "link_gbs": moved / link_secs / 1e9,
