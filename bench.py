@@ -143,13 +143,17 @@ def profile_traffic(kernel_name, src_hash):
         return None
 
 
+# The files that define the forward sweep kernel (tile selection lives elsewhere).
+FWD_KERNEL_SOURCES = ("bulk.cuh", "common.cuh", "ff.cuh", "fwd_sweep.cu", "fwd_sweep.cuh", "kernels.h",
+                      "sweep_core.cuh")
+
+
 def kernel_source_hash():
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2010_01545_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
+    for name in FWD_KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 

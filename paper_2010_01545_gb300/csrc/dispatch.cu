@@ -161,7 +161,9 @@ std::vector<SweepCfg> candidates(int nz, int elem, int vec, int nf) {
       for (int nb : {4, 6, 8, 12}) {
         SweepCfg c{ty, lx, nb, occ};
         const size_t smem = sweep::ring_bytes(nb, (size_t)nf * (ty + 2) * nz * elem);
-        if (smem > 220 * 1024 || smem * (occ == 1 ? 1 : occ) > 225 * 1024) continue;
+        // a ring too large for `occ` CTAs per SM still runs (at fewer CTAs)
+        // and the register cap alone can pay, so only the per-CTA limit prunes
+        if (smem > 220 * 1024) continue;
         if ((uint64_t)nf * (ty + 2) * nz * elem >= (1u << 20)) continue;
         out.push_back(c);
       }
@@ -232,10 +234,13 @@ void select_kernels(advect_ctx& ctx) {
   ctx.sweep = default_sweep(m.nz, elem_of((int)ctx.dtype));
   const int elem = elem_of((int)ctx.dtype);
   if (ctx.dtype == ADVECT_F64_FF && ctx.sweep.ty > 0 && ctx.sweep.ty * (m.nz / sweep_vec(elem)) <= 128) {
-    // double-float arithmetic is bound by the binary32 issue rate: three CTAs
-    // per SM (<= 168 registers, no spills) keep more warps in flight
-    ctx.sweep.occ = 3;
-    while (ctx.sweep.nb > 4 && sweep_smem_bytes(m.nz, elem, ctx.sweep) > 72 * 1024) --ctx.sweep.nb;
+    // double-float arithmetic is bound by the binary32 issue rate: four CTAs
+    // per SM with the code compiled for <= 128 registers (a few spilled
+    // values) and a ring that lets four fit (measured at 2048 x 2048 x 64:
+    // 44.9 Gpts/s with 6 slots, against 43.0 with 7 slots at three CTAs and
+    // 40.9 with the <= 168-register build)
+    ctx.sweep.occ = 4;
+    while (ctx.sweep.nb > 4 && sweep_smem_bytes(m.nz, elem, ctx.sweep) > 56 * 1024) --ctx.sweep.nb;
   }
   sweep_override("ADVECT_SWEEP", ctx.sweep, m.nz, elem, sweep_vec(elem), 3);
   ctx.fwd_kind = ctx.sweep.ty > 0 ? 1 : 0;

@@ -418,6 +418,9 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
     // adds per point) for binary32 arithmetic, where the 3P registers they
     // would hold cost more than the adds.
     constexpr bool kRoll = sizeof(C) != 4;
+    // 8-byte arithmetic (binary64, double-float): re-derive the vertical
+    // halos of the current plane each plane instead of carrying them
+    constexpr bool kRehalo = sizeof(C) == 8;
     constexpr int PS = kRoll ? P : 1;
     C UXM[P], U0[P], UXMYP[P], VXM[P], V0[P], VYM[P], WXM[P], W0[P];
     C SXm[PS], SVm[PS], SWm[PS];
@@ -463,6 +466,17 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
       if (__any_sync(0xffffffffu, timed_out)) break;
       const T* Pc = slot_ptr(pc);
       const T* Pn = slot_ptr(pn);
+      if constexpr (kRehalo) {
+        // the vertical halos of plane i, from its registers (not carried
+        // over from the previous plane: saves their registers)
+        u0m = halo_below<SPLIT, T, C, P>(U0, Pc + o_u0, k0, kb, lane, s_u);
+        u0p = halo_above<SPLIT, T, C, P>(U0, Pc + o_u0, k0, kb, KB, lane, s_u);
+        v0m = halo_below<SPLIT, T, C, P>(V0, Pc + o_v0, k0, kb, lane, s_v);
+        v0p = halo_above<SPLIT, T, C, P>(V0, Pc + o_v0, k0, kb, KB, lane, s_v);
+        vymp = halo_above<SPLIT, T, C, P>(VYM, Pc + o_vm, k0, kb, KB, lane, s_v);
+        w0m = halo_below<SPLIT, T, C, P>(W0, Pc + o_w0, k0, kb, lane, s_w);
+        w0p = halo_above<SPLIT, T, C, P>(W0, Pc + o_w0, k0, kb, KB, lane, s_w);
+      }
       C UXP[P], UYM[P], UYP[P], VXP[P], VYP[P], VXPYM[P], WXP[P], WYM[P], WYP[P];
       IO::ld(Pn + o_u0 + k0, s_u, UXP);
       IO::ld(Pc + o_um + k0, s_u, UYM);
