@@ -386,8 +386,8 @@ def run_e2e(args, torch, op, winds, world, n_pts):
 
 
 def measure_link(torch, h_in, h_out, reps=3):
-    """Seconds for the copies alone: h_in to the device and, at the same time,
-    the device to h_out (pinned, one stream each way)."""
+    """Seconds for the copies alone (best of reps): h_in to the device and, at
+    the same time, the device to h_out (pinned, one stream each way)."""
     d_in = [torch.empty(h.shape, dtype=h.dtype, device="cuda") for h in h_in]
     d_out = [torch.zeros(h.shape, dtype=h.dtype, device="cuda") for h in h_out]
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
@@ -402,10 +402,11 @@ def measure_link(torch, h_in, h_out, reps=3):
         torch.cuda.synchronize()
 
     once()
-    t0 = time.perf_counter()
-    for _ in range(reps):
+    secs = float("inf")
+    for _ in range(reps):  # best of reps: the link's capability, not its noise
+        t0 = time.perf_counter()
         once()
-    secs = (time.perf_counter() - t0) / reps
+        secs = min(secs, time.perf_counter() - t0)
     del d_in, d_out
     torch.cuda.empty_cache()
     return secs
