@@ -487,14 +487,21 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
       IO::ld(Pn + o_w0 + k0, s_w, WXP);
       IO::ld(Pc + o_wm + k0, s_w, WYM);
       IO::ld(Pc + o_wp + k0, s_w, WYP);
-      const C uxpm = halo_below<SPLIT, T, C, P>(UXP, Pn + o_u0, k0, kb, lane, s_u);
-      const C uxpp = halo_above<SPLIT, T, C, P>(UXP, Pn + o_u0, k0, kb, KB, lane, s_u);
-      const C vxpm = halo_below<SPLIT, T, C, P>(VXP, Pn + o_v0, k0, kb, lane, s_v);
-      const C vxpp = halo_above<SPLIT, T, C, P>(VXP, Pn + o_v0, k0, kb, KB, lane, s_v);
+      // halos that plane i reads of the loaded vectors, then (unless they are
+      // re-derived next plane) the ones carried over to plane i+1
       const C wxpm = halo_below<SPLIT, T, C, P>(WXP, Pn + o_w0, k0, kb, lane, s_w);
-      const C wxpp = halo_above<SPLIT, T, C, P>(WXP, Pn + o_w0, k0, kb, KB, lane, s_w);
-      const C vxpymp = halo_above<SPLIT, T, C, P>(VXPYM, Pn + o_vm, k0, kb, KB, lane, s_v);
       const C wypm = halo_below<SPLIT, T, C, P>(WYP, Pc + o_wp, k0, kb, lane, s_w);
+      struct {
+        C um, up, vm, vp, wp, vymp;
+      } nx;
+      if constexpr (!kRehalo) {
+        nx.um = halo_below<SPLIT, T, C, P>(UXP, Pn + o_u0, k0, kb, lane, s_u);
+        nx.up = halo_above<SPLIT, T, C, P>(UXP, Pn + o_u0, k0, kb, KB, lane, s_u);
+        nx.vm = halo_below<SPLIT, T, C, P>(VXP, Pn + o_v0, k0, kb, lane, s_v);
+        nx.vp = halo_above<SPLIT, T, C, P>(VXP, Pn + o_v0, k0, kb, KB, lane, s_v);
+        nx.wp = halo_above<SPLIT, T, C, P>(WXP, Pn + o_w0, k0, kb, KB, lane, s_w);
+        nx.vymp = halo_above<SPLIT, T, C, P>(VXPYM, Pn + o_vm, k0, kb, KB, lane, s_v);
+      }
       // plane i is no longer read from shared memory by this warp
       release(qc, pc);
       pc = pn;
@@ -589,13 +596,15 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
         WXM[q] = W0[q];
         W0[q] = WXP[q];
       }
-      u0m = uxpm;
-      u0p = uxpp;
-      v0m = vxpm;
-      v0p = vxpp;
-      vymp = vxpymp;
-      w0m = wxpm;
-      w0p = wxpp;
+      if constexpr (!kRehalo) {
+        u0m = nx.um;
+        u0p = nx.up;
+        v0m = nx.vm;
+        v0p = nx.vp;
+        vymp = nx.vymp;
+        w0m = wxpm;
+        w0p = nx.wp;
+      }
     }
     ok = !timed_out;
   }
