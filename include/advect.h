@@ -175,9 +175,10 @@ advect_status advect_adjoint(advect_ctx *ctx, const void *u, const void *v, cons
  * nx*ny*nz elements of the context's type (pinned memory gives full copy
  * bandwidth; pageable memory works).  The x range is cut into chunks whose
  * host-to-device copy, kernel and device-to-host copy overlap on internal
- * streams (the chunked transfer proposed in Sec. 6).  Device staging buffers
- * are allocated on the first call and kept by the context.  Returns after
- * the results are in su, sv, sw.
+ * streams (the chunked transfer proposed in Sec. 6); 32 chunks, or
+ * $ADVECT_HOST_CHUNKS (1..64) read when the context is created.  Device
+ * staging buffers are allocated on the first call and kept by the context.
+ * Returns after the results are in su, sv, sw.
  */
 advect_status advect_forward_host(advect_ctx *ctx, const void *u, const void *v, const void *w,
                                   void *su, void *sv, void *sw, const float *scales);

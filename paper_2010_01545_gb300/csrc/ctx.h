@@ -26,8 +26,8 @@ struct HostPath {
   void* d_in[3] = {nullptr, nullptr, nullptr};
   void* d_out[3] = {nullptr, nullptr, nullptr};
   cudaStream_t s_in = nullptr, s_k = nullptr, s_out = nullptr;
-  static constexpr int kMaxChunks = 16;
-  int nchunk = 16;
+  static constexpr int kMaxChunks = 64;
+  int nchunk = 32;  // ADVECT_HOST_CHUNKS (1..64) at create time overrides
   cudaEvent_t ev_in[kMaxChunks] = {};
   cudaEvent_t ev_k[kMaxChunks] = {};
 };

@@ -265,6 +265,10 @@ void select_kernels(advect_ctx& ctx) {
   ctx.fwd_name = ctx.fwd_kind ? "fwd_sweep" : "fwd_point";
   ctx.adj_name = ctx.adj_kind ? "adj_sweep" : "adj_point";
   ctx.tune_fwd = ctx.tune_adj = tune_env_enabled();
+  if (const char* h = getenv("ADVECT_HOST_CHUNKS")) {
+    const int n = atoi(h);
+    if (n >= 1 && n <= HostPath::kMaxChunks) ctx.hp.nchunk = n;
+  }
   if (const char* q = getenv("ADVECT_TEST_SKIP_PLANE")) ctx.test_skip_plane = atoi(q);
   if (const char* b = getenv("ADVECT_TEST_WAIT_CYCLES")) {
     const long long v = atoll(b);
