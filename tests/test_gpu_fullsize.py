@@ -65,6 +65,36 @@ def test_forward_f32_2048x2048x64_sampled(big_winds):
     torch.cuda.empty_cache()
 
 
+def test_forward_f64ff_2048x2048x64_sampled(big_winds):
+    shape = (2048, 2048, 64)
+    op, grid = make_op(shape, "f64ff")
+    outs = op.forward(*(dev(a) for a in big_winds))
+    torch.cuda.synchronize()
+    _check_sample(outs, big_winds, grid, shape, 1e-12, 4)
+    del outs
+    torch.cuda.empty_cache()
+
+
+def test_forward_f16s_2048x2048x64_sampled(big_winds):
+    shape = (2048, 2048, 64)
+    op, grid = make_op(shape, "f16s")
+    s_in = [float(2.0 ** np.ceil(np.log2(np.max(np.abs(a))))) for a in big_winds]
+    s_out = op.output_scales(s_in)
+    h = [(torch.from_numpy(a).cuda() / s).to(torch.float16) for a, s in zip(big_winds, s_in)]
+    deq = [t.to(torch.float64).cpu().numpy() * s for t, s in zip(h, s_in)]
+    outs = op.forward(*h, scales=s_in + s_out)
+    torch.cuda.synchronize()
+    idx = sample_indices(shape, 20000, 5)
+    ref = oracle.forward_points(*deq, oracle.coefficients(grid), idx)
+    for f in range(3):
+        g = outs[f].reshape(-1)[torch.from_numpy(idx).cuda()].to(torch.float64).cpu().numpy() * s_out[f]
+        r = ref[:, f]
+        bound = 2.0 ** -11 * s_out[f] + 2e-6 * np.max(np.abs(r))
+        assert np.max(np.abs(g - r)) <= bound, f"field {f}"
+    del outs, h, deq
+    torch.cuda.empty_cache()
+
+
 def test_integrate_f64_2048x2048x64_in_place_sampled(big_winds):
     """The fused step, in place on a separate base, at the benchmark size."""
     shape = (2048, 2048, 64)
@@ -124,6 +154,21 @@ def test_adjoint_f64_1024x1024x128_dot_product_and_probes():
         # probes away from the periodic seams see their whole neighbourhood
         if all(0 < c < n - 1 for c, n in zip(p[:2], shape[:2])):
             assert abs(fd - jt_h[f][p]) <= 1e-7 * (1 + abs(jt_h[f][p])), (f, p, fd, jt_h[f][p])
+
+
+def test_adjoint_f32_1024x1024x128_against_oracle():
+    """The binary32 adjoint at the differentiation workload's size, in the
+    launch configuration the benchmark uses, against the full FP64 oracle
+    adjoint on the same binary32-rounded inputs."""
+    shape = (1024, 1024, 128)
+    op, grid = make_op(shape, "f32")
+    x = [a.astype(np.float32).astype(np.float64) for a in workload.winds(*shape, seed=45)]
+    lam = [a.astype(np.float32).astype(np.float64) for a in workload.cotangents(*shape, seed=46)]
+    got = [host(t) for t in op.adjoint(*(dev(a, torch.float32) for a in (*x, *lam)))]
+    ref = oracle.adjoint(*x, *lam, oracle.coefficients(grid))
+    for g, r, name in zip(got, ref, ("du", "dv", "dw")):
+        err = float(np.max(np.abs(g - r)) / np.max(np.abs(r)))
+        assert err <= 5e-6, f"{name} normwise error {err:.3e} ({op.kernel_name(True)})"
 
 
 def test_ensemble_48_members_as_benchmarked():
