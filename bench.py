@@ -194,8 +194,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "pw_advection_fwd_2048x2048x64_f64",
-                                            "sample_points_per_step": pts},
+            "data": "synthetic", "config": dict(workload_config(world), sample_points_per_step=pts),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -204,6 +203,13 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- GPU legs
+def workload_config(world):
+    """The benchmarked workload (both arms report it)."""
+    return {"workload": "pw_advection_fwd_2048x2048x64_f64", "nx": SHAPE[0], "ny": SHAPE[1], "nz": SHAPE[2],
+            "points": SHAPE[0] * SHAPE[1] * SHAPE[2], "l2": "inputs (6.4 GB) larger than L2; no flush",
+            "parallelism": f"replicas x{world}"}
+
+
 def whole_job_rate(local_units, local_seconds, device):
     """Units of all ranks over the slowest rank's time (the timed regions are
     bracketed by barriers, so the slowest rank bounds the job)."""
@@ -343,10 +349,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * per_launch, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": "pw_advection_fwd_2048x2048x64_f64", "nx": SHAPE[0],
-                           "ny": SHAPE[1], "nz": SHAPE[2], "points": n_pts,
-                           "l2": "inputs (6.4 GB) larger than L2; no flush",
-                           "parallelism": f"replicas x{world}"},
+                "config": workload_config(world),
                 "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps,
                 "clocks": clk.summary(), "cpu_baseline": cpu, "variants": variants,
                 "kernel_source": src_hash}
