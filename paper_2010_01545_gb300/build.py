@@ -7,6 +7,7 @@ skipped when a stamp of the sources and flags is unchanged.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import glob
 import hashlib
 import os
@@ -41,14 +42,34 @@ def _stamp() -> str:
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link the library if sources changed; returns its path."""
+def _up_to_date(stamp: str) -> bool:
     stamp_path = os.path.join(BUILD, "stamp")
+    if not (os.path.exists(LIB) and os.path.exists(stamp_path)):
+        return False
+    with open(stamp_path) as f:
+        return f.read().strip() == stamp
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile and link the library if sources changed; returns its path.
+    Processes that build at the same time (one per rank) serialise on a lock
+    file; the ones that wait find the library up to date."""
     stamp = _stamp()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp_path):
-        with open(stamp_path) as f:
-            if f.read().strip() == stamp:
+    if not force and _up_to_date(stamp):
+        return LIB
+    os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, "lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and _up_to_date(stamp):
                 return LIB
+            return _compile_and_link(stamp, verbose)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _compile_and_link(stamp: str, verbose: bool) -> str:
+    stamp_path = os.path.join(BUILD, "stamp")
     obj_dir = os.path.join(BUILD, "obj")
     os.makedirs(obj_dir, exist_ok=True)
 
