@@ -367,8 +367,8 @@ def run_e2e(args, torch, op, winds, world, n_pts):
     device while the outputs come back, on two streams, with no kernel."""
     h_in = [torch.from_numpy(a).pin_memory() for a in winds]
     h_out = [torch.empty(SHAPE, dtype=torch.float64).pin_memory() for _ in range(3)]
-    e2e_steps = max(3, min(args.steps, 10))
-    for _ in range(2):
+    e2e_steps = max(3, min(args.steps, 20))
+    for _ in range(args.warmup):
         op.forward_host(*h_in, h_out)
     if world > 1:
         import torch.distributed as dist
@@ -388,6 +388,7 @@ def run_e2e(args, torch, op, winds, world, n_pts):
             "h2d_bytes_per_step": 3 * n_pts * 8, "d2h_bytes_per_step": 3 * n_pts * 8,
             "ms_per_step": 1e3 * e2e_secs,
             "ms_per_step_min": 1e3 * min(per_step), "ms_per_step_median": 1e3 * statistics.median(per_step),
+            "ms_steps": [round(1e3 * x, 2) for x in per_step],
             "link_bound_ms": 1e3 * link_secs, "link_gbs": moved / link_secs / 1e9,
             "link_frac": link_secs / e2e_secs}
 
