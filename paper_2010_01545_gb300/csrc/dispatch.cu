@@ -237,10 +237,10 @@ void select_kernels(advect_ctx& ctx) {
     // double-float arithmetic is bound by the binary32 issue rate: four CTAs
     // per SM with the code compiled for <= 128 registers (a few spilled
     // values) and a ring that lets four fit (measured at 2048 x 2048 x 64:
-    // 44.9 Gpts/s with 6 slots, against 43.0 with 7 slots at three CTAs and
-    // 40.9 with the <= 168-register build)
+    // 48.4 Gpts/s with 5 slots, 47.9 with 6, 44.3 with the <= 168-register
+    // build at three CTAs)
     ctx.sweep.occ = 4;
-    while (ctx.sweep.nb > 4 && sweep_smem_bytes(m.nz, elem, ctx.sweep) > 56 * 1024) --ctx.sweep.nb;
+    while (ctx.sweep.nb > 4 && sweep_smem_bytes(m.nz, elem, ctx.sweep) > 47 * 1024) --ctx.sweep.nb;
   }
   sweep_override("ADVECT_SWEEP", ctx.sweep, m.nz, elem, sweep_vec(elem), 3);
   ctx.fwd_kind = ctx.sweep.ty > 0 ? 1 : 0;

@@ -126,7 +126,7 @@ struct VecIO<f64ff> {
     o[1] = ff(x.y);
   }
   __device__ static __forceinline__ void st(f64ff* g, const C (&v)[P], float) {
-    __stcs(reinterpret_cast<double2*>(g), make_double2((double)v[0], (double)v[1]));
+    __stcs(reinterpret_cast<double2*>(g), make_double2(to_double_fp64(v[0]), to_double_fp64(v[1])));
   }
 };
 
