@@ -44,7 +44,7 @@ FLOP_PER_POINT = 53           # the paper's count for su, sv, sw (Sec. 2.3)
 # per-level vertical products) -- the paper's 53 flops fused.
 FP64_OPS_PER_POINT = 39
 BYTES_PER_POINT = {"f64": 48, "f32": 24, "f16s": 12}       # 3 fields in + 3 out
-ADJ_BYTES_PER_POINT = {"f64": 72, "f32": 36}                # 6 in + 3 out
+ADJ_BYTES_PER_POINT = {"f64": 72, "f32": 36, "f64ff": 72}   # 6 in + 3 out
 ADJ_SHAPE = (1024, 1024, 128)
 FP64_DFMA_PER_CLK_PER_SM = 2   # GB300 nominal (1.25 TFLOP/s FP64); a DFMA throughput probe reached 1.01
 N_SM = 152
@@ -548,7 +548,7 @@ def run_variants(args, torch, torch_api, workload, winds, coeffs, ref_out, strea
     acoef = torch_api.coefficients_from_grid(agrid)
     an = ADJ_SHAPE[0] * ADJ_SHAPE[1] * ADJ_SHAPE[2]
     gen = torch.Generator(device="cuda")
-    for name, tdt in (("f64", torch.float64), ("f32", torch.float32)):
+    for name, tdt in (("f64", torch.float64), ("f32", torch.float32), ("f64ff", torch.float64)):
         gen.manual_seed(workload.DEFAULT_SEED)
         opa = torch_api.Advect(*ADJ_SHAPE, acoef, name)
         x = [torch.rand(ADJ_SHAPE, generator=gen, device="cuda", dtype=tdt) * 20 - 10 for _ in range(3)]

@@ -29,7 +29,8 @@
  * of two binary32 numbers on the binary32 pipes, which on GB300 run 74x the
  * binary64 rate; results agree with binary64 to about 1e-14 normwise (never
  * worse than 1e-12 in the tests) for magnitudes in [2^-80, 2^126]; single
- * grids only (forward, adjoint, host path, no-allocation call).
+ * grids only (forward, integration step, adjoint, host path, no-allocation
+ * call).
  *
  * Memory ownership.  Every buffer pointer is owned by the caller.  Device
  * pointers must be device memory of the current CUDA device, 16-byte aligned
