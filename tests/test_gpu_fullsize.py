@@ -156,19 +156,29 @@ def test_adjoint_f64_1024x1024x128_dot_product_and_probes():
             assert abs(fd - jt_h[f][p]) <= 1e-7 * (1 + abs(jt_h[f][p])), (f, p, fd, jt_h[f][p])
 
 
-def test_adjoint_f32_1024x1024x128_against_oracle():
+def test_adjoint_f32_1024x1024x128_against_oracle_on_blocks():
     """The binary32 adjoint at the differentiation workload's size, in the
-    launch configuration the benchmark uses, against the full FP64 oracle
-    adjoint on the same binary32-rounded inputs."""
+    launch configuration the benchmark uses, against the FP64 oracle adjoint
+    on the same binary32-rounded inputs.  The oracle runs on 34 x 34 x 128
+    blocks cut (periodically) around chosen points -- including the seams of
+    the periodic domain -- and its interior 32 x 32 columns, which see their
+    whole neighbourhood, are compared (keeps the host memory small)."""
     shape = (1024, 1024, 128)
     op, grid = make_op(shape, "f32")
-    x = [a.astype(np.float32).astype(np.float64) for a in workload.winds(*shape, seed=45)]
-    lam = [a.astype(np.float32).astype(np.float64) for a in workload.cotangents(*shape, seed=46)]
-    got = [host(t) for t in op.adjoint(*(dev(a, torch.float32) for a in (*x, *lam)))]
-    ref = oracle.adjoint(*x, *lam, oracle.coefficients(grid))
-    for g, r, name in zip(got, ref, ("du", "dv", "dw")):
-        err = float(np.max(np.abs(g - r)) / np.max(np.abs(r)))
-        assert err <= 5e-6, f"{name} normwise error {err:.3e} ({op.kernel_name(True)})"
+    x = [a.astype(np.float32) for a in workload.winds(*shape, seed=45)]
+    lam = [a.astype(np.float32) for a in workload.cotangents(*shape, seed=46)]
+    got = [host(t) for t in op.adjoint(*(torch.from_numpy(a).cuda() for a in (*x, *lam)))]
+    c = oracle.coefficients(grid)
+    for i0, j0 in ((0, 0), (1023, 511), (500, 1023), (257, 33)):
+        ii = np.arange(i0 - 17, i0 + 17) % shape[0]
+        jj = np.arange(j0 - 17, j0 + 17) % shape[1]
+        blk = [a[np.ix_(ii, jj)].astype(np.float64) for a in (*x, *lam)]
+        ref = oracle.adjoint(*blk, c)
+        for g, r, name in zip(got, ref, ("du", "dv", "dw")):
+            gi = g[np.ix_(ii[1:-1], jj[1:-1])]
+            ri = r[1:-1, 1:-1]
+            err = float(np.max(np.abs(gi - ri)) / np.max(np.abs(ri)))
+            assert err <= 5e-6, f"{name} at ({i0},{j0}): normwise error {err:.3e} ({op.kernel_name(True)})"
 
 
 def test_ensemble_48_members_as_benchmarked():
