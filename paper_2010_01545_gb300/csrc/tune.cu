@@ -4,7 +4,10 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <fcntl.h>
+#include <sys/file.h>
 #include <sys/stat.h>
+#include <unistd.h>
 
 #include "tune.h"
 
@@ -20,9 +23,9 @@ void mkdirs(const std::string& path) {
     if (path[p] == '/') mkdir(path.substr(0, p).c_str(), 0755);
 }
 
-// Parse "key": "value" pairs of a flat JSON object written by save().
-void load_locked() {
-  g_loaded = true;
+// Parse "key": "value" pairs of a flat JSON object written by save_locked()
+// into `into` (entries already there are kept when keep_existing).
+void read_file(std::map<std::string, std::string>& into, bool keep_existing) {
   FILE* f = fopen(tune_cache_path().c_str(), "r");
   if (!f) return;
   std::string text;
@@ -41,15 +44,31 @@ void load_locked() {
     return true;
   };
   std::string k, v;
-  while (read_str(k) && read_str(v)) g_cache[k] = v;
+  while (read_str(k) && read_str(v))
+    if (!keep_existing || !into.count(k)) into[k] = v;
 }
 
+void load_locked() {
+  g_loaded = true;
+  read_file(g_cache, false);
+}
+
+// Write the cache.  Several processes (one per rank) may tune at once: an
+// exclusive lock on a side file serialises them, the file is re-read under
+// the lock so entries other processes wrote are kept, and each process
+// writes its own temporary file before the atomic rename.
 void save_locked() {
   const std::string path = tune_cache_path();
   mkdirs(path);
-  const std::string tmp = path + ".tmp";
+  const int lock = open((path + ".lock").c_str(), O_CREAT | O_RDWR, 0644);
+  if (lock >= 0) flock(lock, LOCK_EX);
+  read_file(g_cache, true);
+  const std::string tmp = path + ".tmp." + std::to_string((long)getpid());
   FILE* f = fopen(tmp.c_str(), "w");
-  if (!f) return;
+  if (!f) {
+    if (lock >= 0) close(lock);
+    return;
+  }
   fprintf(f, "{\n");
   size_t q = 0;
   for (const auto& kv : g_cache)
@@ -57,6 +76,7 @@ void save_locked() {
   fprintf(f, "}\n");
   fclose(f);
   rename(tmp.c_str(), path.c_str());
+  if (lock >= 0) close(lock);  // releases the lock
 }
 
 }  // namespace
