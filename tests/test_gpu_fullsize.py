@@ -1,10 +1,16 @@
 """Parity at the benchmark's full sizes, in the same launch configuration.
 
-The 2048 x 2048 x 64 forward (268M points) runs through the same context
-creation as bench.py; the oracle evaluates a sample of points one by one
-(every boundary class plus random interior points).  The 1024 x 1024 x 128
-adjoint is checked by properties that hold at any size: the dot-product
-identity and central differences at 64 random probes.
+Inputs are drawn on the device (seeded torch generators, the benchmark's
+distributions) so that no multi-gigabyte host arrays are made: heavy host
+memory churn leaves the host's pinned copies stalling for minutes
+afterwards, which would disturb a host-buffer benchmark run after the
+tests.  The oracle evaluates sampled columns exactly: each column's 3 x 3 x nz
+neighbourhood (periodic) is gathered from the device, the neighbourhoods are
+stacked along x in blocks of three planes, and one oracle call returns every
+column's values in the middle plane and row of its block (the middle of a
+block sees only its own block).  The 1024 x 1024 x 128 adjoint is checked by
+properties that hold at any size (dot-product identity, central differences
+at 64 probes) and against the oracle on 34 x 34 x 128 periodic blocks.
 """
 import numpy as np
 import pytest
@@ -12,116 +18,152 @@ import torch
 
 import oracle
 import workload
-from gpu_util import dev, host, make_op
+from gpu_util import host, make_op
 
 pytestmark = pytest.mark.gpu
 
+BIG = (2048, 2048, 64)
 
-def sample_indices(shape, n_random, seed):
-    nx, ny, nz = shape
+
+def device_winds(shape, seed, dtype=torch.float64):
+    """u, v, w ~ U(-10, 10) + 2 sin(2 pi i / nx) cos(2 pi j / ny), on the device."""
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    nx, ny, _ = shape
+    i = torch.arange(nx, device="cuda", dtype=torch.float64)[:, None, None]
+    j = torch.arange(ny, device="cuda", dtype=torch.float64)[None, :, None]
+    pert = 2.0 * torch.sin(2 * np.pi * i / nx) * torch.cos(2 * np.pi * j / ny)
+    out = []
+    for _ in range(3):
+        a = torch.rand(shape, generator=gen, device="cuda", dtype=torch.float64) * 20 - 10
+        a += pert
+        out.append(a.to(dtype))
+    return out
+
+
+def device_normal(shape, seed, n=3, dtype=torch.float64):
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    return [torch.randn(shape, generator=gen, device="cuda", dtype=torch.float64).to(dtype) for _ in range(n)]
+
+
+def sample_columns(shape, n_random, seed):
+    """Random columns plus every boundary class of the periodic grid."""
+    nx, ny, _ = shape
     rng = np.random.default_rng(seed)
-    pts = [(int(rng.integers(nx)), int(rng.integers(ny)), int(rng.integers(nz))) for _ in range(n_random)]
-    for i in (0, 1, nx - 1):
-        for j in (0, ny - 1, ny // 2):
-            for k in (0, 1, 2, nz - 2, nz - 1):
-                pts.append((i, j, k))
-    return np.array([(i * ny + j) * nz + k for i, j, k in pts], dtype=np.int64)
+    cols = [(int(rng.integers(nx)), int(rng.integers(ny))) for _ in range(n_random)]
+    cols += [(i, j) for i in (0, 1, nx - 1) for j in (0, ny // 2, ny - 1)]
+    return cols
 
 
-@pytest.fixture(scope="module")
-def big_winds():
-    return workload.winds(2048, 2048, 64, seed=workload.DEFAULT_SEED)
+def column_blocks(fields, cols, scale=None):
+    """(3N, 3, nz) float64 host arrays, block b (x-planes 3b..3b+2) the
+    periodic 3 x 3 neighbourhood of column b; the oracle's result in plane
+    3b+1, row 1 is that column's."""
+    out = []
+    for f, t in enumerate(fields):
+        nx, ny, nz = t.shape
+        ci = torch.tensor([c[0] for c in cols], device="cuda")
+        cj = torch.tensor([c[1] for c in cols], device="cuda")
+        off = torch.tensor([-1, 0, 1], device="cuda")
+        ii = (ci[:, None] + off[None, :]) % nx
+        jj = (cj[:, None] + off[None, :]) % ny
+        blk = t[ii[:, :, None], jj[:, None, :]].to(torch.float64)  # (N, 3, 3, nz)
+        if scale is not None:
+            blk = blk * scale[f]
+        out.append(blk.reshape(-1, 3, nz).cpu().numpy())
+    return out
 
 
-def _check_sample(outs, winds, grid, shape, tol, seed):
-    idx = sample_indices(shape, 20000, seed)
-    ref = oracle.forward_points(*winds, oracle.coefficients(grid), idx)
+def column_values(t, cols):
+    ci = torch.tensor([c[0] for c in cols], device="cuda")
+    cj = torch.tensor([c[1] for c in cols], device="cuda")
+    return t[ci, cj].to(torch.float64).cpu().numpy()  # (N, nz)
+
+
+def middles(a):
+    return a[1::3, 1, :]
+
+
+def _check_forward(outs, inputs, grid, cols, tol):
+    ref = oracle.forward(*column_blocks(inputs, cols), oracle.coefficients(grid))
     for f in range(3):
-        g = outs[f].reshape(-1)[torch.from_numpy(idx).cuda()].to(torch.float64).cpu().numpy()
-        r = ref[:, f]
+        g = column_values(outs[f], cols)
+        r = middles(ref[f])
         err = np.max(np.abs(g - r)) / np.max(np.abs(r))
         assert err <= tol, f"field {f}: sampled normwise error {err:.3e}"
 
 
-def test_forward_f64_2048x2048x64_sampled(big_winds):
-    shape = (2048, 2048, 64)
-    op, grid = make_op(shape, "f64")
+def test_forward_f64_2048x2048x64_sampled():
+    op, grid = make_op(BIG, "f64")
     assert op.kernel_name() == "fwd_sweep"
-    outs = op.forward(*(dev(a) for a in big_winds))
+    x = device_winds(BIG, workload.DEFAULT_SEED)
+    outs = op.forward(*x)
     torch.cuda.synchronize()
-    _check_sample(outs, big_winds, grid, shape, 1e-12, 1)
-    del outs
-    torch.cuda.empty_cache()
+    _check_forward(outs, x, grid, sample_columns(BIG, 400, 1), 1e-12)
 
 
-def test_forward_f32_2048x2048x64_sampled(big_winds):
-    shape = (2048, 2048, 64)
-    op, grid = make_op(shape, "f32")
-    w32 = [a.astype(np.float32) for a in big_winds]
-    outs = op.forward(*(torch.from_numpy(a).cuda() for a in w32))
+def test_forward_f32_2048x2048x64_sampled():
+    op, grid = make_op(BIG, "f32")
+    x = device_winds(BIG, workload.DEFAULT_SEED, torch.float32)
+    outs = op.forward(*x)
     torch.cuda.synchronize()
-    _check_sample(outs, [a.astype(np.float64) for a in w32], grid, shape, 2e-6, 2)
-    del outs
-    torch.cuda.empty_cache()
+    _check_forward(outs, x, grid, sample_columns(BIG, 400, 2), 2e-6)
 
 
-def test_forward_f64ff_2048x2048x64_sampled(big_winds):
-    shape = (2048, 2048, 64)
-    op, grid = make_op(shape, "f64ff")
-    outs = op.forward(*(dev(a) for a in big_winds))
+def test_forward_f64ff_2048x2048x64_sampled():
+    op, grid = make_op(BIG, "f64ff")
+    x = device_winds(BIG, workload.DEFAULT_SEED + 1)
+    outs = op.forward(*x)
     torch.cuda.synchronize()
-    _check_sample(outs, big_winds, grid, shape, 1e-12, 4)
-    del outs
-    torch.cuda.empty_cache()
+    _check_forward(outs, x, grid, sample_columns(BIG, 400, 4), 1e-12)
 
 
-def test_forward_f16s_2048x2048x64_sampled(big_winds):
-    shape = (2048, 2048, 64)
-    op, grid = make_op(shape, "f16s")
-    s_in = [float(2.0 ** np.ceil(np.log2(np.max(np.abs(a))))) for a in big_winds]
+def test_forward_f16s_2048x2048x64_sampled():
+    op, grid = make_op(BIG, "f16s")
+    x = device_winds(BIG, workload.DEFAULT_SEED + 2)
+    s_in = [float(2.0 ** np.ceil(np.log2(torch.max(torch.abs(a)).item()))) for a in x]
     s_out = op.output_scales(s_in)
-    h = [(torch.from_numpy(a).cuda() / s).to(torch.float16) for a, s in zip(big_winds, s_in)]
-    deq = [t.to(torch.float64).cpu().numpy() * s for t, s in zip(h, s_in)]
+    h = [(a / s).to(torch.float16) for a, s in zip(x, s_in)]
+    del x
     outs = op.forward(*h, scales=s_in + s_out)
     torch.cuda.synchronize()
-    idx = sample_indices(shape, 20000, 5)
-    ref = oracle.forward_points(*deq, oracle.coefficients(grid), idx)
+    cols = sample_columns(BIG, 400, 5)
+    ref = oracle.forward(*column_blocks(h, cols, s_in), oracle.coefficients(grid))
     for f in range(3):
-        g = outs[f].reshape(-1)[torch.from_numpy(idx).cuda()].to(torch.float64).cpu().numpy() * s_out[f]
-        r = ref[:, f]
+        g = column_values(outs[f], cols) * s_out[f]
+        r = middles(ref[f])
         bound = 2.0 ** -11 * s_out[f] + 2e-6 * np.max(np.abs(r))
         assert np.max(np.abs(g - r)) <= bound, f"field {f}"
-    del outs, h, deq
-    torch.cuda.empty_cache()
 
 
-def test_integrate_f64_2048x2048x64_in_place_sampled(big_winds):
+def test_integrate_f64_2048x2048x64_in_place_sampled():
     """The fused step, in place on a separate base, at the benchmark size."""
-    shape = (2048, 2048, 64)
-    op, grid = make_op(shape, "f64")
-    base = workload.winds(*shape, seed=workload.DEFAULT_SEED + 7)
+    op, grid = make_op(BIG, "f64")
+    x = device_winds(BIG, workload.DEFAULT_SEED)
+    b = device_winds(BIG, workload.DEFAULT_SEED + 7)
+    cols = sample_columns(BIG, 400, 3)
+    bblk = column_blocks(b, cols)
     dt = 0.37
-    x = [dev(a) for a in big_winds]
-    b = [dev(a) for a in base]
     out = op.integrate(*x, dt, base=b, out=b)
     torch.cuda.synchronize()
-    idx = sample_indices(shape, 20000, 3)
-    s = oracle.forward_points(*big_winds, oracle.coefficients(grid), idx)
+    c = oracle.coefficients(grid)
+    xblk = column_blocks(x, cols)
+    ref = oracle.integrate(*xblk, c, dt, base=bblk)
+    s = oracle.forward(*xblk, c)
     for f in range(3):
-        g = out[f].reshape(-1)[torch.from_numpy(idx).cuda()].cpu().numpy()
-        r = base[f].reshape(-1)[idx] + dt * s[:, f]
-        bound = 1e-12 * dt * np.max(np.abs(s[:, f])) + 2.0 ** -51 * np.max(np.abs(r))
+        g = column_values(out[f], cols)
+        r = middles(ref[f])
+        bound = 1e-12 * dt * np.max(np.abs(middles(s[f]))) + 2.0 ** -51 * np.max(np.abs(r))
         assert np.max(np.abs(g - r)) <= bound, f"field {f}"
-    del x, b, out
-    torch.cuda.empty_cache()
 
 
 def test_adjoint_f64_1024x1024x128_dot_product_and_probes():
     shape = (1024, 1024, 128)
     op, _ = make_op(shape, "f64")
-    x = [dev(a) for a in workload.winds(*shape, seed=41)]
-    d = [dev(a) for a in workload.cotangents(*shape, seed=42)]
-    lam = [dev(a) for a in workload.cotangents(*shape, seed=43)]
+    x = device_winds(shape, 41)
+    d = device_normal(shape, 42)
+    lam = device_normal(shape, 43)
     h = 2.0 ** -10
     fp = op.forward(*(a + h * b for a, b in zip(x, d)))
     fm = op.forward(*(a - h * b for a, b in zip(x, d)))
@@ -133,7 +175,6 @@ def test_adjoint_f64_1024x1024x128_dot_product_and_probes():
     mag = sum(torch.sum(torch.abs(a * b)).item() for a, b in zip(d, jt))
     assert abs(lhs - rhs) <= 1e-10 * mag
     del jd, d
-    jt_h = [host(t) for t in jt]
     rng = np.random.default_rng(44)
     eps = 1e-6
     out_p = op.forward(*x)
@@ -153,29 +194,30 @@ def test_adjoint_f64_1024x1024x128_dot_product_and_probes():
         fd = sum(torch.sum((a - b) * l[sl]).item() for a, b, l in zip(plus, minus, lam)) / (2 * eps)
         # probes away from the periodic seams see their whole neighbourhood
         if all(0 < c < n - 1 for c, n in zip(p[:2], shape[:2])):
-            assert abs(fd - jt_h[f][p]) <= 1e-7 * (1 + abs(jt_h[f][p])), (f, p, fd, jt_h[f][p])
+            jt_p = jt[f][p].item()
+            assert abs(fd - jt_p) <= 1e-7 * (1 + abs(jt_p)), (f, p, fd, jt_p)
 
 
 def test_adjoint_f32_1024x1024x128_against_oracle_on_blocks():
     """The binary32 adjoint at the differentiation workload's size, in the
     launch configuration the benchmark uses, against the FP64 oracle adjoint
-    on the same binary32-rounded inputs.  The oracle runs on 34 x 34 x 128
-    blocks cut (periodically) around chosen points -- including the seams of
-    the periodic domain -- and its interior 32 x 32 columns, which see their
-    whole neighbourhood, are compared (keeps the host memory small)."""
+    on the same binary32 inputs, on 34 x 34 x 128 blocks cut (periodically)
+    around chosen points -- including the seams of the periodic domain --
+    whose interior 32 x 32 columns see their whole neighbourhood."""
     shape = (1024, 1024, 128)
     op, grid = make_op(shape, "f32")
-    x = [a.astype(np.float32) for a in workload.winds(*shape, seed=45)]
-    lam = [a.astype(np.float32) for a in workload.cotangents(*shape, seed=46)]
-    got = [host(t) for t in op.adjoint(*(torch.from_numpy(a).cuda() for a in (*x, *lam)))]
+    x = device_winds(shape, 45, torch.float32)
+    lam = device_normal(shape, 46, dtype=torch.float32)
+    got = op.adjoint(*x, *lam)
+    torch.cuda.synchronize()
     c = oracle.coefficients(grid)
     for i0, j0 in ((0, 0), (1023, 511), (500, 1023), (257, 33)):
-        ii = np.arange(i0 - 17, i0 + 17) % shape[0]
-        jj = np.arange(j0 - 17, j0 + 17) % shape[1]
-        blk = [a[np.ix_(ii, jj)].astype(np.float64) for a in (*x, *lam)]
+        ii = torch.arange(i0 - 17, i0 + 17, device="cuda") % shape[0]
+        jj = torch.arange(j0 - 17, j0 + 17, device="cuda") % shape[1]
+        blk = [t[ii[:, None], jj[None, :]].to(torch.float64).cpu().numpy() for t in (*x, *lam)]
         ref = oracle.adjoint(*blk, c)
         for g, r, name in zip(got, ref, ("du", "dv", "dw")):
-            gi = g[np.ix_(ii[1:-1], jj[1:-1])]
+            gi = g[ii[1:-1, None], jj[None, 1:-1]].to(torch.float64).cpu().numpy()
             ri = r[1:-1, 1:-1]
             err = float(np.max(np.abs(gi - ri)) / np.max(np.abs(ri)))
             assert err <= 5e-6, f"{name} at ({i0},{j0}): normwise error {err:.3e} ({op.kernel_name(True)})"
@@ -184,7 +226,7 @@ def test_adjoint_f32_1024x1024x128_against_oracle_on_blocks():
 def test_ensemble_48_members_as_benchmarked():
     """The 48-member FP32 ensemble of the benchmark (autotuned, one persistent
     launch per direction): every member's forward against the oracle on
-    sampled points, every member's adjoint bitwise against the single-grid
+    sampled columns, every member's adjoint bitwise against the single-grid
     adjoint, and the three smallest members' adjoints fully against the
     oracle."""
     from gpu_util import ensure_built, lib_coeffs, oracle_adjoint
@@ -202,15 +244,13 @@ def test_ensemble_48_members_as_benchmarked():
     y = ens.forward(*x)
     g = ens.adjoint(*x, *lam)
     torch.cuda.synchronize()
-    rng = np.random.default_rng(7)
     for m, s in enumerate(shapes):
-        xm = [f[m].to(torch.float64).cpu().numpy() for f in x]
-        n = s[0] * s[1] * s[2]
-        idx = np.unique(np.concatenate([rng.integers(0, n, 1500), np.arange(s[2]), n - 1 - np.arange(s[2])]))
-        ref = oracle.forward_points(*xm, oracle.coefficients(grids[m]), idx)
+        cols = sample_columns(s, 60, 7 + m)
+        ref = oracle.forward(*column_blocks([f[m] for f in x], cols), oracle.coefficients(grids[m]))
         for f in range(3):
-            got = y[f][m].reshape(-1)[torch.from_numpy(idx).cuda()].to(torch.float64).cpu().numpy()
-            err = np.max(np.abs(got - ref[:, f])) / max(np.max(np.abs(ref[:, f])), 1e-30)
+            got = column_values(y[f][m], cols)
+            r = middles(ref[f])
+            err = np.max(np.abs(got - r)) / max(np.max(np.abs(r)), 1e-30)
             assert err <= 2e-6, (m, s, f, err)
         op = torch_api.Advect(*s, coeffs[m], "f32")
         single = op.adjoint(*(f[m] for f in x), *(f[m] for f in lam))
@@ -222,6 +262,6 @@ def test_ensemble_48_members_as_benchmarked():
         lm = [f[m].to(torch.float64).cpu().numpy() for f in lam]
         ref = oracle_adjoint(*xm, *lm, grids[m])
         for f in range(3):
-            got = g[f][m].to(torch.float64).cpu().numpy()
+            got = host(g[f][m])
             err = np.max(np.abs(got - ref[f])) / np.max(np.abs(ref[f]))
             assert err <= 5e-6, (m, f, err)
