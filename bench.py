@@ -266,11 +266,16 @@ def main():
     ap.add_argument("--adjoint", action="store_true", help="--shape case runs the adjoint")
     ap.add_argument("--integrate", action="store_true",
                     help="--shape case runs the forward fused with the integration step")
+    ap.add_argument("--ensemble", type=int, default=0,
+                    help="run only an ensemble of this many members (FP32, forward, or adjoint with "
+                         "--adjoint; the default tiles), for profiling")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.ensemble:
+        return run_ensemble_case(args)
     if args.shape:
         return run_case(args)
 
@@ -565,6 +570,36 @@ def run_variants(args, torch, torch_api, workload, winds, coeffs, ref_out, strea
         torch.cuda.empty_cache()
     out["ensemble_f32_48"] = run_ensemble(args, torch, torch_api, workload, stream, hbm_gbs)
     return out
+
+
+def run_ensemble_case(args):
+    """The first N members of the benchmark's ensemble (FP32), forward or
+    adjoint, for profiling the persistent ensemble kernel on a small case."""
+    import torch
+
+    import workload
+    from paper_2010_01545_gb300 import build, torch_api
+    build.build()
+    shapes = workload.ensemble_shapes(48)[: args.ensemble]
+    pts = sum(a * b * c for a, b, c in shapes)
+    coeffs = [torch_api.coefficients_from_grid(workload.vertical_grid(s[2])) for s in shapes]
+    ens = torch_api.AdvectEnsemble(shapes, coeffs, "f32")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(workload.DEFAULT_SEED)
+    x = [[torch.rand(s, generator=gen, device="cuda") * 20 - 10 for s in shapes] for _ in range(3)]
+    lam = [[torch.randn(s, generator=gen, device="cuda") for s in shapes] for _ in range(3)]
+    out = [ens.empty() for _ in range(3)]
+    if args.adjoint:
+        call = lambda: ens.adjoint(*x, *lam, out=out)  # noqa: E731
+    else:
+        call = lambda: ens.forward(*x, out=out)  # noqa: E731
+    for _ in range(args.warmup):
+        call()
+    secs = time_calls(call, args.steps, torch.cuda.current_stream()) / args.steps
+    print(json.dumps({"case": f"ensemble_{'adj' if args.adjoint else 'fwd'}_f32_{len(shapes)}_members",
+                      "points": pts, "tile": ens.tuned_config(bool(args.adjoint)), "ms": 1e3 * secs,
+                      "points_per_s": pts / secs, "steps": args.steps, "warmup": args.warmup}), flush=True)
+    return 0
 
 
 def run_ensemble(args, torch, torch_api, workload, stream, hbm_gbs):
