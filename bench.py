@@ -22,6 +22,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -148,12 +149,20 @@ FWD_KERNEL_SOURCES = ("bulk.cuh", "common.cuh", "ff.cuh", "fwd_sweep.cu", "fwd_s
                       "sweep_core.cuh")
 
 
+def _code_only(text: str) -> str:
+    """Source text without comments and whitespace (a comment edit does not
+    change the kernel)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "".join(text.split())
+
+
 def kernel_source_hash():
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2010_01545_gb300", "csrc")
     for name in FWD_KERNEL_SOURCES:
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(csrc, name)) as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

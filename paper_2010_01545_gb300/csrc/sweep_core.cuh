@@ -14,12 +14,13 @@
 //
 // Thread (row rr, k-block kb) owns P consecutive levels of one column for the
 // whole tile.  The own-row values of planes i-1 and i, the off-row values
-// reused one plane later, and the face sums shared between consecutive
-// planes stay in registers; vertical neighbours come from the adjacent lanes
-// by shuffle.  Each plane then costs nine vector loads from shared memory per
-// thread.  Per point the arithmetic and its order follow Listing 1 (Sec. 2.1)
-// for su and the same pattern for sv and sw; the lid branch comes from
-// tzc2[nz-1] == 0 and zero values above the top level.
+// reused one plane later, and (for 8-byte arithmetic; binary32 recomputes
+// them) the face sums shared between consecutive planes stay in registers;
+// vertical neighbours come from the adjacent lanes by shuffle.  Each plane
+// then costs nine vector loads from shared memory per thread.  Per point the
+// arithmetic and its order follow Listing 1 (Sec. 2.1) for su and the same
+// pattern for sv and sw; the lid branch comes from tzc2[nz-1] == 0 and zero
+// values above the top level.
 #pragma once
 
 #include <type_traits>
