@@ -103,6 +103,16 @@ def test_forward_f64_2048x2048x64_sampled():
     _check_forward(outs, x, grid, sample_columns(BIG, 400, 1), 1e-12)
 
 
+@pytest.mark.parametrize("shape", [(512, 512, 64), (1024, 1024, 64)])
+def test_forward_f64_sweep_sizes_sampled(shape):
+    """The smaller grids of the very-large-grid sweep."""
+    op, grid = make_op(shape, "f64")
+    x = device_winds(shape, workload.DEFAULT_SEED + 11)
+    outs = op.forward(*x)
+    torch.cuda.synchronize()
+    _check_forward(outs, x, grid, sample_columns(shape, 400, 9), 1e-12)
+
+
 def test_forward_f32_2048x2048x64_sampled():
     op, grid = make_op(BIG, "f32")
     x = device_winds(BIG, workload.DEFAULT_SEED, torch.float32)
