@@ -167,17 +167,32 @@ def kernel_source_hash():
 
 
 # ----------------------------------------------------------------- oracle legs
-def oracle_sample_rate(winds, grid, planes, repeats=1):
+def oracle_sample_rate(winds, grid, planes, repeats=1, openmp=False):
     import oracle
     c = oracle.coefficients(grid)
     sub = [np.ascontiguousarray(a[: planes + 2]) for a in winds]   # planes + x-halo
     best = None
     for _ in range(repeats):
         t0 = time.perf_counter()
-        oracle.forward(*sub, c, i_range=(1, planes + 1))
+        oracle.forward(*sub, c, i_range=(1, planes + 1), openmp=openmp)
         dt = time.perf_counter() - t0
         best = dt if best is None else min(best, dt)
     return planes * SHAPE[1] * SHAPE[2] / best, best
+
+
+def oracle_all_cores(winds, grid, planes):
+    """The same oracle loop built with -fopenmp (x-planes shared among all
+    host cores; bitwise the same results), timed on the same sample."""
+    import subprocess as sp
+    import oracle
+    try:
+        oracle.build(openmp=True)
+    except (sp.CalledProcessError, OSError) as e:
+        return {"unavailable": f"gcc -fopenmp build failed: {e}"}
+    oracle_sample_rate(winds, grid, min(8, planes), openmp=True)    # thread-pool start
+    rate, dt = oracle_sample_rate(winds, grid, planes, repeats=2, openmp=True)
+    return {"value": rate, "unit": UNIT, "cores": oracle.threads(openmp=True), "kind": "oracle",
+            "sample": f"the same {planes} x-planes, OpenMP parallel-for over x ({dt:.2f} s, best of 2)"}
 
 
 def run_reference(args):
@@ -357,7 +372,8 @@ def main():
         rate, dt = oracle_sample_rate(winds, grid, SHAPE[0] - 2)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"FP64 forward over {SHAPE[0] - 2} of the 2048 x-planes of the same grid "
-                         f"({dt:.1f} s, single-threaded plain C, -O2 -ffp-contract=off)"}
+                         f"({dt:.1f} s, single-threaded plain C, -O2 -ffp-contract=off)",
+               "all_cores": oracle_all_cores(winds, grid, SHAPE[0] - 2)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -40,30 +40,36 @@ _SRC = os.path.join(_HERE, "advect_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c99", "-fPIC", "-shared"]
 
-_lib_handle = None
+OPENMP_CFLAGS = ["-fopenmp"]
+
+_lib_handles = {}
 
 
-def _lib_path() -> str:
+def _lib_path(openmp: bool = False) -> str:
+    flags = CFLAGS + (OPENMP_CFLAGS if openmp else [])
     with open(_SRC, "rb") as f:
-        tag = hashlib.sha1(f.read() + " ".join(CFLAGS).encode()).hexdigest()[:12]
-    return os.path.join(_BUILD, f"liboracle_{platform.machine()}_{tag}.so")
+        tag = hashlib.sha1(f.read() + " ".join(flags).encode()).hexdigest()[:12]
+    kind = "_omp" if openmp else ""
+    return os.path.join(_BUILD, f"liboracle{kind}_{platform.machine()}_{tag}.so")
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (idempotent); returns the .so path."""
-    path = _lib_path()
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with gcc (idempotent); returns the .so path.  With
+    ``openmp`` the same source is built with -fopenmp, which shares the
+    forward's x-planes among all host cores (same results, bit for bit)."""
+    path = _lib_path(openmp)
     if force or not os.path.exists(path):
         os.makedirs(_BUILD, exist_ok=True)
         tmp = path + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", *CFLAGS, "-o", tmp, _SRC], check=True)
+        flags = CFLAGS + (OPENMP_CFLAGS if openmp else [])
+        subprocess.run(["gcc", *flags, "-o", tmp, _SRC], check=True)
         os.replace(tmp, path)
     return path
 
 
-def _lib():
-    global _lib_handle
-    if _lib_handle is None:
-        lib = ctypes.CDLL(build())
+def _lib(openmp: bool = False):
+    if openmp not in _lib_handles:
+        lib = ctypes.CDLL(build(openmp=openmp))
         dp = ctypes.POINTER(ctypes.c_double)
         lib.oracle_coefficients.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                             dp, dp, dp, dp, dp, dp, dp, dp, dp]
@@ -78,8 +84,15 @@ def _lib():
         lib.oracle_adjoint.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [dp] * 4
                                        + [dp] * 9)
         lib.oracle_adjoint.restype = ctypes.c_int
-        _lib_handle = lib
-    return _lib_handle
+        lib.oracle_threads.argtypes = []
+        lib.oracle_threads.restype = ctypes.c_int
+        _lib_handles[openmp] = lib
+    return _lib_handles[openmp]
+
+
+def threads(openmp: bool = False) -> int:
+    """Threads ``forward`` runs on (1 for the plain build)."""
+    return int(_lib(openmp).oracle_threads())
 
 
 def _p(a: np.ndarray):
@@ -131,15 +144,16 @@ def _check_fields(*fields):
     return shape
 
 
-def forward(u, v, w, c: Coefficients, i_range=None):
-    """(su, sv, sw) for x-planes in ``i_range`` (default: all; others stay 0)."""
+def forward(u, v, w, c: Coefficients, i_range=None, openmp=False):
+    """(su, sv, sw) for x-planes in ``i_range`` (default: all; others stay 0).
+    ``openmp`` runs the same loop on all host cores (the -fopenmp build)."""
     u, v, w = _f64(u), _f64(v), _f64(w)
     nx, ny, nz = _check_fields(u, v, w)
     if nz != c.nz:
         raise ValueError("coefficient tables do not match nz")
     i0, i1 = (0, nx) if i_range is None else i_range
     su, sv, sw = (np.zeros((nx, ny, nz)) for _ in range(3))
-    rc = _lib().oracle_forward(nx, ny, nz, c.tcx, c.tcy, _p(c.tzc1), _p(c.tzc2), _p(c.tzd1),
+    rc = _lib(openmp).oracle_forward(nx, ny, nz, c.tcx, c.tcy, _p(c.tzc1), _p(c.tzc2), _p(c.tzd1),
                                _p(c.tzd2), _p(u), _p(v), _p(w), _p(su), _p(sv), _p(sw), i0, i1)
     if rc != 0:
         raise ValueError("oracle_forward: invalid arguments")

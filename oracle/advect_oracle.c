@@ -45,6 +45,9 @@
  */
 #include <stddef.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define AT(i, j, k) ((((size_t)(i)) * (size_t)ny + (size_t)(j)) * (size_t)nz + (size_t)(k))
 
@@ -126,7 +129,10 @@ static void point(int nx, int ny, int nz, double tcx, double tcy,
     *out_sw = sw;
 }
 
-/* Forward over the x-planes i in [i_begin, i_end); other planes untouched. */
+/* Forward over the x-planes i in [i_begin, i_end); other planes untouched.
+ * Every point is computed on its own from the inputs, so the x-planes may be
+ * shared out among threads: built with -fopenmp the loop over i runs on all
+ * host cores and gives the same bits as the single-threaded build. */
 int oracle_forward(int nx, int ny, int nz, double tcx, double tcy,
                    const double *tzc1, const double *tzc2, const double *tzd1, const double *tzd2,
                    const double *u, const double *v, const double *w,
@@ -134,6 +140,7 @@ int oracle_forward(int nx, int ny, int nz, double tcx, double tcy,
 {
     if (nx < 1 || ny < 1 || nz < 3 || i_begin < 0 || i_end > nx || i_begin > i_end)
         return 1;
+#pragma omp parallel for schedule(static)
     for (int i = i_begin; i < i_end; ++i)
         for (int j = 0; j < ny; ++j)
             for (int k = 0; k < nz; ++k)
@@ -160,6 +167,16 @@ int oracle_forward_points(int nx, int ny, int nz, double tcx, double tcy,
               &out[3 * p], &out[3 * p + 1], &out[3 * p + 2]);
     }
     return 0;
+}
+
+/* Threads oracle_forward uses: 1 unless built with -fopenmp. */
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* ---- adjoint (scatter) ---------------------------------------------------- */

@@ -34,3 +34,15 @@ def test_kernel_source_hash_covers_existing_files():
     for name in bench.FWD_KERNEL_SOURCES:
         assert os.path.exists(os.path.join(csrc, name)), name
     assert re.fullmatch(r"[0-9a-f]{16}", bench.kernel_source_hash())
+
+
+def test_all_cores_oracle_leg_reports_threads_and_rate():
+    import workload
+    grid = workload.vertical_grid(bench.SHAPE[2])
+    planes = 6
+    winds = [workload.wind_field(planes + 2, bench.SHAPE[1], bench.SHAPE[2], f) for f in range(3)]
+    leg = bench.oracle_all_cores(winds, grid, planes)
+    if "unavailable" in leg:
+        return
+    assert leg["cores"] >= 1 and leg["value"] > 0 and leg["unit"] == bench.UNIT
+    assert f"{planes} x-planes" in leg["sample"]

@@ -77,10 +77,10 @@ def test_pins_catch_planted_mistake(mutation, source, tmp_path):
     src.write_text(source.replace(old, new))
     so = tmp_path / "mutant.so"
     subprocess.run(["gcc", *oracle.CFLAGS, "-o", str(so), str(src)], check=True)
-    saved = oracle._lib_handle
-    oracle._lib_handle = None
+    saved = dict(oracle._lib_handles)
+    oracle._lib_handles.clear()
     real_build = oracle.build
-    oracle.build = lambda force=False: str(so)
+    oracle.build = lambda force=False, openmp=False: str(so)
     caught = []
     try:
         for name, fn, kwargs in _pins():
@@ -90,7 +90,8 @@ def test_pins_catch_planted_mistake(mutation, source, tmp_path):
                 caught.append(name)
     finally:
         oracle.build = real_build
-        oracle._lib_handle = saved
+        oracle._lib_handles.clear()
+        oracle._lib_handles.update(saved)
     assert caught, f"no pin caught mutation {mutation}"
 
 
