@@ -210,8 +210,8 @@ cudaError_t tune_single(advect_ctx& ctx, int adj, const FwdArgs* fa, const AdjAr
   if (!(adj && ctx.dtype == ADVECT_F16S)) {
     for (const SweepCfg& c : candidates(m.nz, elem, vec, nf)) {
       const float ms = time_ms(st, [&]() {
-        return adj ? launch_adj_sweep((int)ctx.dtype, *aa, c, ctx.d_flag, st)
-                   : launch_fwd_sweep((int)ctx.dtype, *fa, c, ctx.d_flag, st);
+        return adj ? launch_adj_sweep((int)ctx.dtype, *aa, fit_planes(c, aa->s.nx), ctx.d_flag, st)
+                   : launch_fwd_sweep((int)ctx.dtype, *fa, fit_planes(c, fa->i1 - fa->i0), ctx.d_flag, st);
       }, e);
       if (e != cudaSuccess) return e;
       if (ms < best_ms) {
@@ -279,14 +279,14 @@ void select_kernels(advect_ctx& ctx) {
 cudaError_t launch_fwd(const advect_ctx& ctx, const FwdArgs& a, cudaStream_t st) {
   if (ctx.fwd_kind == 1 && aligned16(a.u) && aligned16(a.v) && aligned16(a.w) && aligned16(a.su) &&
       aligned16(a.sv) && aligned16(a.sw) && aligned16(a.bu) && aligned16(a.bv) && aligned16(a.bw))
-    return launch_fwd_sweep((int)ctx.dtype, a, ctx.sweep, ctx.d_flag, st);
+    return launch_fwd_sweep((int)ctx.dtype, a, fit_planes(ctx.sweep, a.i1 - a.i0), ctx.d_flag, st);
   return launch_fwd_point((int)ctx.dtype, a, st);
 }
 
 cudaError_t launch_adj(const advect_ctx& ctx, const AdjArgs& a, cudaStream_t st) {
   if (ctx.adj_kind == 1 && aligned16(a.u) && aligned16(a.v) && aligned16(a.w) && aligned16(a.dsu) &&
       aligned16(a.dsv) && aligned16(a.dsw) && aligned16(a.du) && aligned16(a.dv) && aligned16(a.dw))
-    return launch_adj_sweep((int)ctx.dtype, a, ctx.adj_sweep, ctx.d_flag, st);
+    return launch_adj_sweep((int)ctx.dtype, a, fit_planes(ctx.adj_sweep, a.s.nx), ctx.d_flag, st);
   return launch_adj_point((int)ctx.dtype, a, st);
 }
 

@@ -166,7 +166,7 @@ extern "C" advect_status advect_forward_noalloc(int nx, int ny, int nz, const ad
   a.i0 = 0;
   a.i1 = nx;
   int* flag = reinterpret_cast<int*>(scratch);
-  const SweepCfg cfg = default_sweep(nz, (int)eb);
+  const SweepCfg cfg = fit_planes(default_sweep(nz, (int)eb), nx);
   auto al16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
   cudaError_t e;
   if (cfg.ty > 0 && al16(u) && al16(v) && al16(w) && al16(su) && al16(sv) && al16(sw))
