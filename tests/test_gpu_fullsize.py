@@ -168,6 +168,60 @@ def test_integrate_f64_2048x2048x64_in_place_sampled():
         assert np.max(np.abs(g - r)) <= bound, f"field {f}"
 
 
+def test_integrate_f32_2048x2048x64_in_place_sampled():
+    """The binary32 step as the benchmark runs it: a separate base (a copy of
+    the winds) updated in place, dt = 0.5."""
+    op, grid = make_op(BIG, "f32")
+    x = device_winds(BIG, workload.DEFAULT_SEED + 8, torch.float32)
+    b = [t.clone() for t in x]
+    cols = sample_columns(BIG, 400, 6)
+    bblk = column_blocks(b, cols)
+    dt = 0.5
+    op.integrate(*x, dt, base=b, out=b)
+    torch.cuda.synchronize()
+    c = oracle.coefficients(grid)
+    xblk = column_blocks(x, cols)
+    ref = oracle.integrate(*xblk, c, dt, base=bblk)
+    s = oracle.forward(*xblk, c)
+    for f in range(3):
+        g = column_values(b[f], cols)
+        r = middles(ref[f])
+        bound = 2e-6 * dt * np.max(np.abs(middles(s[f]))) + 2.0 ** -22 * np.max(np.abs(r))
+        assert np.max(np.abs(g - r)) <= bound, f"field {f}"
+
+
+def _adjoint_blocks(op, grid, x, lam, got, tol):
+    """The adjoint against the FP64 oracle adjoint on 34 x 34 x nz blocks cut
+    (periodically) around chosen points, seams included; an output depends
+    only on inputs within one point in x and y, so each block's interior
+    32 x 32 columns are the grid's own."""
+    shape = tuple(x[0].shape)
+    c = oracle.coefficients(grid)
+    for i0, j0 in ((0, 0), (shape[0] - 1, shape[1] // 2), (shape[0] // 2, shape[1] - 1), (257, 33)):
+        ii = torch.arange(i0 - 17, i0 + 17, device="cuda") % shape[0]
+        jj = torch.arange(j0 - 17, j0 + 17, device="cuda") % shape[1]
+        blk = [t[ii[:, None], jj[None, :]].to(torch.float64).cpu().numpy() for t in (*x, *lam)]
+        ref = oracle.adjoint(*blk, c)
+        for g, r, name in zip(got, ref, ("du", "dv", "dw")):
+            gi = g[ii[1:-1, None], jj[None, 1:-1]].to(torch.float64).cpu().numpy()
+            ri = r[1:-1, 1:-1]
+            err = float(np.max(np.abs(gi - ri)) / np.max(np.abs(ri)))
+            assert err <= tol, f"{name} at ({i0},{j0}): normwise error {err:.3e} ({op.kernel_name(True)})"
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f64ff"])
+def test_adjoint_binary64_1024x1024x128_against_oracle_on_blocks(dtype):
+    """The binary64-storage adjoints at the differentiation workload's size,
+    in the benchmark's launch configuration, within the 1e-12 bar."""
+    shape = (1024, 1024, 128)
+    op, grid = make_op(shape, dtype)
+    x = device_winds(shape, 47)
+    lam = device_normal(shape, 48)
+    got = op.adjoint(*x, *lam)
+    torch.cuda.synchronize()
+    _adjoint_blocks(op, grid, x, lam, got, 1e-12)
+
+
 def test_adjoint_f64_1024x1024x128_dot_product_and_probes():
     shape = (1024, 1024, 128)
     op, _ = make_op(shape, "f64")
