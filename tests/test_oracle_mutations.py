@@ -43,6 +43,28 @@ MUTATIONS = {
     "tzd_uses_w_spacing": ("double dznk1 = zn[k + 1] - zn[k];", "double dznk1 = z[k + 1] - z[k];"),
     "adjoint_product_rule_operand": ("gc[cc] += s * fa[a];", "gc[cc] += s * fb[b];"),
     "adjoint_cotangent_index": ("l = dsv[q]; /* sv terms */", "l = dsu[q]; /* sv terms */"),
+    "sv_y_upper_sign_flip": ("- v[AT(i, jp, k)] * (v[AT(i, j, k)] + v[AT(i, jp, k)]));",
+                             "+ v[AT(i, jp, k)] * (v[AT(i, j, k)] + v[AT(i, jp, k)]));"),
+    "sv_upper_vertical_wrong_column": (
+        "- tzc2[k] * v[AT(i, j, k + 1)] * (w[AT(i, j, k)] + w[AT(i, jp, k)]);",
+        "- tzc2[k] * v[AT(i, j, k + 1)] * (w[AT(i, j, k)] + w[AT(i, j, k)]);"),
+    "sw_x_lower_wrong_level": ("sw = tcx * (w[AT(im, j, k)] * (u[AT(im, j, k)] + u[AT(im, j, k + 1)])",
+                               "sw = tcx * (w[AT(im, j, k)] * (u[AT(im, j, k)] + u[AT(im, j, k - 1)])"),
+    "sw_y_upper_wrong_row": ("- w[AT(i, jp, k)] * (v[AT(i, j, k)] + v[AT(i, j, k + 1)]));",
+                             "- w[AT(i, jp, k)] * (v[AT(i, jp, k)] + v[AT(i, j, k + 1)]));"),
+    "sw_lower_vertical_wrong_operand": ("sw = sw + tzd1[k] * w[AT(i, j, k - 1)] *",
+                                        "sw = sw + tzd1[k] * w[AT(i, j, k)] *"),
+    "tzd2_density_level": ("tzd2[k] = rhon[k + 1] /", "tzd2[k] = rhon[k] /"),
+    "tzc2_density": ("tzc2[k] = rho[k] / (4.0 * dzk * rhon[k]);",
+                     "tzc2[k] = rhon[k] / (4.0 * dzk * rhon[k]);"),
+    "adjoint_su_y_target_swapped": (
+        "term(tcy, l, u, AT(i, jm, k), v, AT(i, jm, k), v, AT(ip, jm, k), du, dv, dv);",
+        "term(tcy, l, u, AT(i, jm, k), v, AT(i, jm, k), v, AT(ip, jm, k), du, dv, du);"),
+    "adjoint_sw_vertical_coefficient": ("term(tzd1[k], l, w, AT(i, j, k - 1)",
+                                        "term(tzd2[k], l, w, AT(i, j, k - 1)"),
+    "adjoint_sv_x_index": (
+        "term(-tcx, l, v, AT(ip, j, k), u, AT(i, j, k), u, AT(i, jp, k), dv, du, du);",
+        "term(-tcx, l, v, AT(ip, j, k), u, AT(i, j, k), u, AT(ip, jp, k), dv, du, du);"),
 }
 
 
