@@ -60,3 +60,17 @@ def exchange_x_halos(slabs, group=None) -> None:
             req.wait()
         s[0] = recv_left
         s[-1] = recv_right
+
+
+def fill_x_halos_local(slabs_by_rank) -> None:
+    """The same exchange for sub-domains held by one process (several slabs
+    on one device, e.g. to run a decomposed grid on fewer GPUs than ranks):
+    slabs_by_rank[r] is rank r's list of padded slabs (one per field); halo
+    plane 0 of rank r takes the last owned plane of rank r-1 and halo plane
+    -1 the first owned plane of rank r+1 (periodic)."""
+    world = len(slabs_by_rank)
+    for r in range(world):
+        left, right = slabs_by_rank[(r - 1) % world], slabs_by_rank[(r + 1) % world]
+        for s, sl, sr in zip(slabs_by_rank[r], left, right):
+            s[0] = sl[-2]
+            s[-1] = sr[1]
