@@ -209,6 +209,13 @@ __device__ __forceinline__ void add_step(const T* base, size_t o, float scale, c
   for (int q = 0; q < P; ++q) s[q] = b[q] + dt * s[q];
 }
 
+// Pull one base vector of the integration step into L2 ahead of its load
+// (addresses inside the base field only; no registers held).
+template <typename T, int P>
+__device__ __forceinline__ void prefetch_base(const T* base, size_t o) {
+  if (base) asm volatile("prefetch.global.L2 [%0];" ::"l"(base + o));
+}
+
 // Bulk-copy plane ql of the tile (x index i_lo-1+ql, periodic) into its slot;
 // NF fields (t.nf == NF).
 template <int NF, typename T>
@@ -460,6 +467,18 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
       }
     }
     const bool f64z = sizeof(C) == 4 && t.f64_levels > 0 && k0 <= t.f64_levels;
+    // integration: the base vectors of the next plane are pulled into L2 one
+    // plane ahead of their streaming loads in the epilogue
+    const size_t plane_elems = (size_t)ny * nz;
+    const size_t o_row = (size_t)j * nz + k0;
+    if constexpr (INTEG) {
+      if (row_ok && t.i_lo < t.i_hi) {
+        const size_t o = (size_t)t.i_lo * plane_elems + o_row;
+        prefetch_base<T, P>(t.b[0], o);
+        prefetch_base<T, P>(t.b[1], o);
+        prefetch_base<T, P>(t.b[2], o);
+      }
+    }
 
     for (int i = t.i_lo; i < t.i_hi; ++i) {
       const int qc = i - t.i_lo + 1;  // plane i (plane i+1 is qc + 1)
@@ -477,6 +496,14 @@ __device__ bool forward_tile(const Tile<T>& t, const Ring& R, int* flag) {
         vymp = halo_above<SPLIT, T, C, P>(VYM, Pc + o_vm, k0, kb, KB, lane, s_v);
         w0m = halo_below<SPLIT, T, C, P>(W0, Pc + o_w0, k0, kb, lane, s_w);
         w0p = halo_above<SPLIT, T, C, P>(W0, Pc + o_w0, k0, kb, KB, lane, s_w);
+      }
+      if constexpr (INTEG) {
+        if (row_ok && i + 1 < t.i_hi) {
+          const size_t o = (size_t)(i + 1) * plane_elems + o_row;
+          prefetch_base<T, P>(t.b[0], o);
+          prefetch_base<T, P>(t.b[1], o);
+          prefetch_base<T, P>(t.b[2], o);
+        }
       }
       C UXP[P], UYM[P], UYP[P], VXP[P], VYP[P], VXPYM[P], WXP[P], WYM[P], WYP[P];
       IO::ld(Pn + o_u0 + k0, s_u, UXP);
