@@ -36,7 +36,8 @@
  * pointers must be device memory of the current CUDA device, 16-byte aligned
  * for the fast paths (any alignment of the element size is accepted).  The
  * library copies coefficient tables at create time and keeps no pointer to
- * caller memory after a call returns.  Inputs must not overlap outputs.
+ * caller memory after a call returns.  Inputs must not overlap outputs or
+ * outputs each other; inputs may share memory (they are only read).
  *
  * Streams and errors.  Device calls are asynchronous on the given stream
  * (NULL = legacy default stream).  Every call returns an advect_status;
