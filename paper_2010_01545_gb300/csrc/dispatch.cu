@@ -252,10 +252,11 @@ void select_kernels(advect_ctx& ctx) {
   ctx.adj_sweep = default_adj_sweep(m.nz, elem);
   if (ctx.dtype == ADVECT_F64_FF && ctx.adj_sweep.ty > 0) {
     // double-float adjoint: 128-plane tiles where the grid still gives at
-    // least four CTAs per resident slot on 152 SMs (measured at 1024 x 1024 x
-    // 128: 16.2 against 15.8 Gpts/s with 64-plane tiles)
+    // least eight CTAs per resident slot on 152 SMs (measured: 16.2 against
+    // 15.8 Gpts/s at 1024 x 1024 x 128; at 512 x 512 x 128, four per slot,
+    // 2.23 against 2.19 ms, so smaller grids keep 64-plane tiles)
     const long long ctas = (long long)((m.nx + 127) / 128) * ((m.ny + ctx.adj_sweep.ty - 1) / ctx.adj_sweep.ty);
-    if (ctas >= 4LL * 152 * ctx.adj_sweep.occ) ctx.adj_sweep.lx = 128;
+    if (ctas >= 8LL * 152 * ctx.adj_sweep.occ) ctx.adj_sweep.lx = 128;
   }
   sweep_override("ADVECT_ADJ_SWEEP", ctx.adj_sweep, m.nz, elem, adj_sweep_vec(elem), 6);
   ctx.adj_kind = ctx.adj_sweep.ty > 0 ? 1 : 0;
