@@ -47,7 +47,11 @@ FP64_OPS_PER_POINT = 39
 BYTES_PER_POINT = {"f64": 48, "f32": 24, "f16s": 12}       # 3 fields in + 3 out
 ADJ_BYTES_PER_POINT = {"f64": 72, "f32": 36, "f64ff": 72}   # 6 in + 3 out
 ADJ_SHAPE = (1024, 1024, 128)
-FP64_DFMA_PER_CLK_PER_SM = 2   # GB300 nominal (1.25 TFLOP/s FP64); a DFMA throughput probe reached 1.01
+# binary64 operations of the gather-form adjoint per point, as its three sums
+# are written (each multiply-add fused; no sums shared between points): 28 for
+# du, 28 for dv, 30 for dw and the three doublings 2u, 2v, 2w
+FP64_ADJ_OPS_PER_POINT = 89
+FP64_DFMA_PER_CLK_PER_SM = 2   # GB300 nominal (1.25 TFLOP/s FP64)
 N_SM = 152
 
 
@@ -164,6 +168,30 @@ def kernel_source_hash():
         with open(os.path.join(csrc, name)) as f:
             h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
+
+
+def fp64_pipe_rate():
+    """The binary64 pipe's measured rate on this GPU (G fused multiply-adds
+    per second) from the in-tree probe kernel (probe/fp64_rate.cu), timed
+    with CUDA events: best of three runs of ~10 ms each."""
+    import ctypes
+    from paper_2010_01545_gb300 import build
+    lib = ctypes.CDLL(build.PROBE_LIB)
+    f = lib.advect_probe_fp64_fma_rate
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                  ctypes.POINTER(ctypes.c_double)]
+    f.restype = ctypes.c_int
+    best = None
+    for _ in range(3):
+        g, ms = ctypes.c_double(), ctypes.c_double()
+        rc = f(2048, 4, 5, ctypes.byref(g), ctypes.byref(ms))
+        if rc != 0:
+            raise RuntimeError(f"fp64 probe failed (CUDA error {rc})")
+        if best is None or g.value > best[0]:
+            best = (g.value, ms.value)
+    return {"gops": best[0], "kernel_ms": best[1],
+            "how": "8 independent DFMA chains per thread, 4 x 256-thread CTAs per SM, 2048 iterations; "
+                   "best of 3 runs of 5 launches (CUDA events)"}
 
 
 # ----------------------------------------------------------------- oracle legs
@@ -338,7 +366,9 @@ def main():
     fwd_name = op.kernel_name()
 
     hbm_gbs, sm_max_mhz, peak_kind = peaks()
-    fp64_peak_gops = FP64_DFMA_PER_CLK_PER_SM * N_SM * sm_max_mhz * 1e6 / 1e9
+    nominal_gops = FP64_DFMA_PER_CLK_PER_SM * N_SM * sm_max_mhz * 1e6 / 1e9
+    probe = fp64_pipe_rate()
+    fp64_peak_gops = probe["gops"]
     achieved_gops = FP64_OPS_PER_POINT * n_pts / per_launch / 1e9
     achieved_gflops = FLOP_PER_POINT * n_pts / per_launch / 1e9
     achieved_gbs = BYTES_PER_POINT["f64"] * n_pts / per_launch / 1e9
@@ -347,7 +377,11 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved_gops, "peak": fp64_peak_gops,
                 "unit": "G FP64 op/s", "frac": achieved_gops / fp64_peak_gops, "traffic": traffic,
                 "kernel": fwd_name, "tile": op.tuned_config(),
-                "peak_kind": "FP64 pipe: 2 add/mul/fma per clk per SM x 152 SM x max SM clock",
+                "peak_kind": "measured: binary64 pipe throughput probe on this GPU (one op per DFMA)",
+                "peak_probe": probe,
+                "peak_nominal": nominal_gops,
+                "frac_of_nominal": achieved_gops / nominal_gops,
+                "nominal_kind": "2 add/mul/fma per clk per SM x 152 SM x max SM clock",
                 "ops_per_point": FP64_OPS_PER_POINT,
                 "flops": {"achieved": achieved_gflops, "peak": 2 * fp64_peak_gops, "unit": "GFLOP/s",
                           "frac": achieved_gflops / (2 * fp64_peak_gops),
@@ -364,7 +398,7 @@ def main():
     variants = {}
     if not args.no_variants:
         variants = run_variants(args, torch, torch_api, workload, winds, coeffs, ref_out, stream,
-                                hbm_gbs, grid)
+                                hbm_gbs, grid, fp64_peak_gops)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -381,8 +415,9 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": workload_config(world),
                 "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps,
-                "clocks": clk.summary(), "cpu_baseline": cpu, "variants": variants,
-                "kernel_source": src_hash}
+                "clocks": clk.summary(), "cpu_baseline": cpu,
+                "cpu_baseline_all_cores": cpu.get("all_cores") if cpu else None,
+                "variants": variants, "kernel_source": src_hash}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -493,7 +528,8 @@ def run_case(args):
     return 0
 
 
-def run_variants(args, torch, torch_api, workload, winds, coeffs, ref_out, stream, hbm_gbs, grid):
+def run_variants(args, torch, torch_api, workload, winds, coeffs, ref_out, stream, hbm_gbs, grid,
+                 fp64_peak_gops):
     out = {}
     n_pts = SHAPE[0] * SHAPE[1] * SHAPE[2]
     steps = max(3, min(args.steps, 10))
@@ -587,10 +623,15 @@ def run_variants(args, torch, torch_api, workload, winds, coeffs, ref_out, strea
         for _ in range(args.warmup):
             opa.adjoint(*x, *lam, out=g)
         secs = time_calls(lambda: opa.adjoint(*x, *lam, out=g), steps, stream) / steps
-        out[f"adjoint_{name}_1024x1024x128"] = {
+        rec = out[f"adjoint_{name}_1024x1024x128"] = {
             "value": an / secs, "unit": UNIT, "ms": 1e3 * secs, "kernel": opa.kernel_name(True),
             "tile": opa.tuned_config(True),
             "hbm_frac": ADJ_BYTES_PER_POINT[name] * an / secs / 1e9 / hbm_gbs}
+        if name == "f64":
+            gops = FP64_ADJ_OPS_PER_POINT * an / secs / 1e9
+            rec["alu"] = {"bound": "alu", "ops_per_point": FP64_ADJ_OPS_PER_POINT, "achieved": gops,
+                          "peak": fp64_peak_gops, "unit": "G FP64 op/s", "frac": gops / fp64_peak_gops,
+                          "peak_kind": "measured: binary64 pipe throughput probe on this GPU"}
         del x, lam, g, opa
         torch.cuda.empty_cache()
     out["ensemble_f32_48"] = run_ensemble(args, torch, torch_api, workload, stream, hbm_gbs)

@@ -127,7 +127,8 @@ advect_status advect_create(int nx, int ny, int nz, const advect_coeffs *c, adve
  * u, v, w.  Device pointers, layout as above, element type of the context.
  * scales: ADVECT_F16S only, host array of 6 floats -- input scales of u, v, w
  * then output scales of su, sv, sw (stored value = true value / scale; use
- * advect_f16s_output_scales for a safe choice); NULL for other types.
+ * advect_f16s_output_scales for a safe choice); every scale must be a
+ * positive, finite power of two (EINVAL otherwise); NULL for other types.
  */
 advect_status advect_forward(advect_ctx *ctx, const void *u, const void *v, const void *w,
                              void *su, void *sv, void *sw, const float *scales,
@@ -249,7 +250,8 @@ const char *advect_tuned_config(const advect_ctx *ctx, int adjoint);
  * Arguments are those of advect_create plus advect_forward: shape, host
  * coefficient tables, element type, device fields (u, v, w in; su, sv, sw
  * out; owned by the caller), F16S scales, stream.  Results equal
- * advect_forward's for the same inputs (the same kernels run).
+ * advect_forward's for the same inputs bit for bit (the same kernels run,
+ * with the tile a new context of that type starts from).
  *
  * Scratch: the coefficient tables and the kernels' error flag live in one
  * fixed library array in device memory (ADVECT_NOALLOC_MAX_NZ levels,
@@ -263,8 +265,10 @@ const char *advect_tuned_config(const advect_ctx *ctx, int adjoint);
  * context API where those reports matter.
  *
  * The first call made on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture on that device.
+ * (cudaGetSymbolAddress) and caches it with the device's current driver
+ * context; make that first call before any stream capture on that device.
+ * After cudaDeviceReset, or under another context, the next call looks the
+ * address up again (make it, too, outside a capture).
  *
  * EINVAL if nz > ADVECT_NOALLOC_MAX_NZ, or for the argument errors of
  * advect_create / advect_forward.

@@ -77,10 +77,6 @@ def _lib(openmp: bool = False):
         lib.oracle_forward.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [dp] * 4
                                        + [dp] * 6 + [ctypes.c_int] * 2)
         lib.oracle_forward.restype = ctypes.c_int
-        lib.oracle_forward_points.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_double] * 2
-                                              + [dp] * 4 + [dp] * 3 + [ctypes.c_longlong,
-                                                                        ctypes.POINTER(ctypes.c_longlong), dp])
-        lib.oracle_forward_points.restype = ctypes.c_int
         lib.oracle_adjoint.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [dp] * 4
                                        + [dp] * 9)
         lib.oracle_adjoint.restype = ctypes.c_int
@@ -158,21 +154,6 @@ def forward(u, v, w, c: Coefficients, i_range=None, openmp=False):
     if rc != 0:
         raise ValueError("oracle_forward: invalid arguments")
     return su, sv, sw
-
-
-def forward_points(u, v, w, c: Coefficients, flat_index):
-    """(n, 3) array of (su, sv, sw) at the given flat indices of (nx, ny, nz)."""
-    u, v, w = _f64(u), _f64(v), _f64(w)
-    nx, ny, nz = _check_fields(u, v, w)
-    idx = np.ascontiguousarray(flat_index, dtype=np.int64)
-    out = np.zeros((idx.shape[0], 3))
-    rc = _lib().oracle_forward_points(
-        nx, ny, nz, c.tcx, c.tcy, _p(c.tzc1), _p(c.tzc2), _p(c.tzd1), _p(c.tzd2),
-        _p(u), _p(v), _p(w), idx.shape[0], idx.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
-        _p(out))
-    if rc != 0:
-        raise ValueError("oracle_forward_points: index out of range")
-    return out
 
 
 def adjoint(u, v, w, dsu, dsv, dsw, c: Coefficients):

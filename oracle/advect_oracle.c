@@ -149,26 +149,6 @@ int oracle_forward(int nx, int ny, int nz, double tcx, double tcy,
     return 0;
 }
 
-/* Forward at n chosen flat indices; out holds (su, sv, sw) per index. */
-int oracle_forward_points(int nx, int ny, int nz, double tcx, double tcy,
-                          const double *tzc1, const double *tzc2, const double *tzd1,
-                          const double *tzd2, const double *u, const double *v, const double *w,
-                          long long n, const long long *flat, double *out)
-{
-    long long total = (long long)nx * ny * nz;
-    for (long long p = 0; p < n; ++p) {
-        long long f = flat[p];
-        if (f < 0 || f >= total)
-            return 1;
-        int k = (int)(f % nz);
-        int j = (int)((f / nz) % ny);
-        int i = (int)(f / ((long long)nz * ny));
-        point(nx, ny, nz, tcx, tcy, tzc1, tzc2, tzd1, tzd2, u, v, w, i, j, k,
-              &out[3 * p], &out[3 * p + 1], &out[3 * p + 2]);
-    }
-    return 0;
-}
-
 /* Threads oracle_forward uses: 1 unless built with -fopenmp. */
 int oracle_threads(void)
 {

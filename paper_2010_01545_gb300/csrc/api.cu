@@ -54,8 +54,8 @@ bool valid_dtype(int d) { return d == ADVECT_F64 || d == ADVECT_F32 || d == ADVE
 
 // Host copy of one member's tables with the entries no formula reads set to
 // zero, and tzc2[nz-1] = 0 (Listing 1 drops the upper flux at the top).
-void masked_tables(const advect_coeffs* c, int nz, std::vector<double>& t) {
-  t.assign(4 * (size_t)nz, 0.0);
+void masked_tables(const advect_coeffs* c, int nz, double* t) {
+  for (size_t q = 0; q < 4 * (size_t)nz; ++q) t[q] = 0.0;
   for (int k = 1; k < nz; ++k) {
     t[k] = c->tzc1[k];
     if (k < nz - 1) t[nz + k] = c->tzc2[k];
@@ -66,7 +66,23 @@ void masked_tables(const advect_coeffs* c, int nz, std::vector<double>& t) {
   }
 }
 
+void masked_tables(const advect_coeffs* c, int nz, std::vector<double>& t) {
+  t.resize(4 * (size_t)nz);
+  masked_tables(c, nz, t.data());
+}
+
 bool is_finite(double x) { return std::isfinite(x); }
+
+// F16S scales: positive, finite powers of two (the sweep folds the input
+// scales into the constants, which is exact only for powers of two).
+advect_status check_f16s_scales(const float* s, int n) {
+  for (int q = 0; q < n; ++q) {
+    int e = 0;
+    if (!(s[q] > 0.f) || !std::isfinite(s[q]) || std::frexp(s[q], &e) != 0.5f)
+      return fail(ADVECT_EINVAL, "scale %d (%g) must be a positive, finite power of two", q, (double)s[q]);
+  }
+  return ADVECT_OK;
+}
 
 advect_status check_coeffs(const advect_coeffs* c, int nz) {
   if (!c) return fail(ADVECT_EINVAL, "coefficients pointer is NULL");
@@ -187,19 +203,14 @@ advect_status read_scales(advect_ctx* ctx, const float* scales, Scales& sc, bool
   if (!scales)
     return fail(ADVECT_EINVAL, with_base ? "F16S needs 9 scales (u, v, w, 3 outputs, 3 bases)"
                                          : "F16S needs 6 scales (u, v, w, su, sv, sw)");
-  for (int q = 0; q < 6; ++q)
-    if (!(scales[q] > 0.f) || !std::isfinite(scales[q]))
-      return fail(ADVECT_EINVAL, "scale %d must be positive and finite", q);
+  advect_status s = check_f16s_scales(scales, with_base ? 9 : 6);
+  if (s) return s;
   for (int q = 0; q < 3; ++q) {
     sc.in[q] = scales[q];
     sc.inv_out[q] = 1.f / scales[3 + q];
   }
-  if (with_base) {
-    for (int q = 6; q < 9; ++q)
-      if (!(scales[q] > 0.f) || !std::isfinite(scales[q]))
-        return fail(ADVECT_EINVAL, "scale %d must be positive and finite", q);
+  if (with_base)
     for (int q = 0; q < 3; ++q) sc.base[q] = scales[6 + q];
-  }
   return ADVECT_OK;
 }
 
@@ -287,6 +298,8 @@ advect_status advect_create(int nx, int ny, int nz, const advect_coeffs* c, adve
   if (!ctx) return fail(ADVECT_ENOMEM, "host allocation failed");
   ctx->dtype = dtype;
   CUDA_TRY(cudaGetDevice(&ctx->device), "cudaGetDevice");
+  CUDA_TRY(cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device),
+           "cudaDeviceGetAttribute");
   ctx->members.resize(1);
   ctx->members[0].nx = nx;
   ctx->members[0].ny = ny;

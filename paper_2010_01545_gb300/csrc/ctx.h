@@ -38,6 +38,7 @@ struct advect_ctx {
   bool ensemble = false;
   advect_dtype dtype = ADVECT_F64;
   int device = 0;
+  int sms = 152;  // multiprocessors of the device (read at create time)
   int f64_levels = 0;
   int* d_flag = nullptr;  // device error flag (non-zero: a bounded wait gave up)
   std::vector<advect::Member> members;
@@ -73,6 +74,9 @@ namespace advect {
 // Kernel selection and launch (dispatch.cu).
 void select_kernels(advect_ctx& ctx);
 SweepCfg default_sweep(int nz, int elem);  // ty == 0: the shape cannot use the plane sweep
+// The forward tile a new context of this element type (Dtype) starts from,
+// before the tuning cache or an environment override.
+SweepCfg default_fwd_sweep(int nz, int dtype);
 // A sweep launch is (ceil(ny / ty), ceil(planes / lx)) CTAs and gridDim.y is
 // at most 65535, so an x extent longer than 65535 tiles takes longer tiles.
 inline SweepCfg fit_planes(SweepCfg c, int planes) {

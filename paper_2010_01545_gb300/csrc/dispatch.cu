@@ -233,30 +233,37 @@ cudaError_t tune_single(advect_ctx& ctx, int adj, const FwdArgs* fa, const AdjAr
   return cudaSuccess;
 }
 
-void select_kernels(advect_ctx& ctx) {
-  const Member& m = ctx.members[0];
-  ctx.sweep = default_sweep(m.nz, elem_of((int)ctx.dtype));
-  const int elem = elem_of((int)ctx.dtype);
-  if (ctx.dtype == ADVECT_F64_FF && ctx.sweep.ty > 0 && ctx.sweep.ty * (m.nz / sweep_vec(elem)) <= 128) {
+SweepCfg default_fwd_sweep(int nz, int dtype) {
+  const int elem = elem_of(dtype);
+  SweepCfg c = default_sweep(nz, elem);
+  if (dtype == kF64FF && c.ty > 0 && c.ty * (nz / sweep_vec(elem)) <= 128) {
     // double-float arithmetic is bound by the binary32 issue rate: four CTAs
     // per SM with the code compiled for <= 128 registers (a few spilled
     // values) and a ring that lets four fit (measured at 2048 x 2048 x 64:
     // 48.4 Gpts/s with 5 slots, 47.9 with 6, 44.3 with the <= 168-register
     // build at three CTAs)
-    ctx.sweep.occ = 4;
-    while (ctx.sweep.nb > 4 && sweep_smem_bytes(m.nz, elem, ctx.sweep) > 47 * 1024) --ctx.sweep.nb;
+    c.occ = 4;
+    while (c.nb > 4 && sweep_smem_bytes(nz, elem, c) > 47 * 1024) --c.nb;
   }
+  return c;
+}
+
+void select_kernels(advect_ctx& ctx) {
+  const Member& m = ctx.members[0];
+  const int elem = elem_of((int)ctx.dtype);
+  ctx.sweep = default_fwd_sweep(m.nz, (int)ctx.dtype);
   sweep_override("ADVECT_SWEEP", ctx.sweep, m.nz, elem, sweep_vec(elem), 3);
   ctx.fwd_kind = ctx.sweep.ty > 0 ? 1 : 0;
   ctx.fwd_name = ctx.fwd_kind ? "fwd_sweep" : "fwd_point";
   ctx.adj_sweep = default_adj_sweep(m.nz, elem);
   if (ctx.dtype == ADVECT_F64_FF && ctx.adj_sweep.ty > 0) {
     // double-float adjoint: 128-plane tiles where the grid still gives at
-    // least eight CTAs per resident slot on 152 SMs (measured: 16.2 against
-    // 15.8 Gpts/s at 1024 x 1024 x 128; at 512 x 512 x 128, four per slot,
-    // 2.23 against 2.19 ms, so smaller grids keep 64-plane tiles)
+    // least eight CTAs per resident slot on the device's SMs (measured on
+    // 152 SMs: 16.2 against 15.8 Gpts/s at 1024 x 1024 x 128; at 512 x 512 x
+    // 128, four per slot, 2.23 against 2.19 ms, so smaller grids keep
+    // 64-plane tiles)
     const long long ctas = (long long)((m.nx + 127) / 128) * ((m.ny + ctx.adj_sweep.ty - 1) / ctx.adj_sweep.ty);
-    if (ctas >= 8LL * 152 * ctx.adj_sweep.occ) ctx.adj_sweep.lx = 128;
+    if (ctas >= 8LL * ctx.sms * ctx.adj_sweep.occ) ctx.adj_sweep.lx = 128;
   }
   sweep_override("ADVECT_ADJ_SWEEP", ctx.adj_sweep, m.nz, elem, adj_sweep_vec(elem), 6);
   ctx.adj_kind = ctx.adj_sweep.ty > 0 ? 1 : 0;

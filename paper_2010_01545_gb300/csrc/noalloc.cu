@@ -15,13 +15,16 @@
 // as long as the library stays loaded.  A one-block set-up kernel, which
 // receives the tables by value as a kernel parameter, writes them there and
 // clears the flag before each forward launch on the caller's stream; then
-// the ordinary forward kernel (plane sweep or point kernel, exactly as
-// advect_forward would choose by default) runs with pointers into the array.
+// the ordinary forward kernel (plane sweep or point kernel, with the tile a
+// new context of the same type starts from) runs with pointers into the
+// array.
 //
 // In host code the array's name is only a stand-in for the symbol, not a
-// device address: its address on a device is looked up once per device with
-// cudaGetSymbolAddress (on the first call made with that device current) and
-// cached.
+// device address: its address on a device is looked up with
+// cudaGetSymbolAddress on the first call made with that device current, and
+// cached together with the device's current context, so that after a
+// cudaDeviceReset (or under another context) the next call looks it up again
+// instead of using a stale address.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -65,16 +68,40 @@ __global__ void noalloc_setup_kernel(SetupParams p) {
 
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {};
+void* g_scratch_ctx[kMaxDevices] = {};  // the driver context the address belongs to
 
-// Device address of the scratch on the current device (looked up once).
+// The driver's current context (cuCtxGetCurrent through the runtime's entry
+// point lookup, so the library links no driver library); NULL if unknown.
+void* current_driver_context() {
+  using Fn = int (*)(void**);
+  static Fn fn = []() -> Fn {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return reinterpret_cast<Fn>(f);
+  }();
+  void* c = nullptr;
+  if (fn && fn(&c) != 0) c = nullptr;
+  return c;
+}
+
+// Device address of the scratch on the current device: looked up on the
+// first call with this device current and again whenever the device's
+// current context has changed since (e.g. after cudaDeviceReset).
 advect_status scratch_address(int device, unsigned char** out) {
   if (device < 0 || device >= kMaxDevices) return fail(ADVECT_EUNSUPPORTED, "device ordinal %d too large", device);
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_addr[device]) {
+  void* cur = current_driver_context();
+  if (!g_scratch_addr[device] || cur != g_scratch_ctx[device]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress of the no-allocation scratch");
     g_scratch_addr[device] = p;
+    g_scratch_ctx[device] = current_driver_context();  // the lookup may have created the context
   }
   *out = static_cast<unsigned char*>(g_scratch_addr[device]);
   return ADVECT_OK;
@@ -101,9 +128,8 @@ extern "C" advect_status advect_forward_noalloc(int nx, int ny, int nz, const ad
   }
   if (dtype == ADVECT_F16S) {
     if (!scales) return fail(ADVECT_EINVAL, "F16S needs 6 scales (u, v, w, su, sv, sw)");
-    for (int q = 0; q < 6; ++q)
-      if (!(scales[q] > 0.f) || !std::isfinite(scales[q]))
-        return fail(ADVECT_EINVAL, "scale %d must be positive and finite", q);
+    s = check_f16s_scales(scales, 6);
+    if (s) return s;
     for (int q = 0; q < 3; ++q) {
       sc.in[q] = scales[q];
       sc.inv_out[q] = 1.f / scales[3 + q];
@@ -134,15 +160,7 @@ extern "C" advect_status advect_forward_noalloc(int nx, int ny, int nz, const ad
   // tzc2[nz-1] = 0 (Listing 1 drops the upper flux at the lid).
   SetupParams sp;
   sp.nz = nz;
-  for (int q = 0; q < 4 * nz; ++q) sp.t[q] = 0.0;
-  for (int k = 1; k < nz; ++k) {
-    sp.t[k] = c->tzc1[k];
-    if (k < nz - 1) sp.t[nz + k] = c->tzc2[k];
-  }
-  for (int k = 1; k < nz - 1; ++k) {
-    sp.t[2 * nz + k] = c->tzd1[k];
-    sp.t[3 * nz + k] = c->tzd2[k];
-  }
+  masked_tables(c, nz, sp.t);
   cudaStream_t st = (cudaStream_t)stream;
   noalloc_setup_kernel<<<1, 256, 0, st>>>(sp);
   ADVECT_CUDA_TRY(cudaGetLastError(), "no-allocation set-up kernel");
@@ -166,7 +184,7 @@ extern "C" advect_status advect_forward_noalloc(int nx, int ny, int nz, const ad
   a.i0 = 0;
   a.i1 = nx;
   int* flag = reinterpret_cast<int*>(scratch);
-  const SweepCfg cfg = fit_planes(default_sweep(nz, (int)eb), nx);
+  const SweepCfg cfg = fit_planes(default_fwd_sweep(nz, (int)dtype), nx);
   auto al16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
   cudaError_t e;
   if (cfg.ty > 0 && al16(u) && al16(v) && al16(w) && al16(su) && al16(sv) && al16(sw))

@@ -144,3 +144,18 @@ def test_ensemble_create_validates_on_the_host(lib):
     assert lib.advect_ensemble_forward(None, *([None] * 6), None) == 1
     assert lib.advect_autotune(None, 1) == 1
     assert lib.advect_tuned_config(None, 0) == b""
+
+
+@pytest.mark.parametrize("bad", [3.0, 0.75, 0.0, -2.0, float("inf"), float("nan")])
+def test_f16s_scales_must_be_powers_of_two(lib, bad):
+    """The F16S sweep folds the input scales into the constants, which is
+    exact only for powers of two: any other scale is rejected (checked before
+    any CUDA call, so no GPU is needed)."""
+    c = _coeffs(8)
+    scales = [16.0, 16.0, 8.0, 64.0, 64.0, 32.0]
+    for q in (0, 4):
+        s = list(scales)
+        s[q] = bad
+        with pytest.raises(_abi.AdvectError) as e:
+            _abi.advect_forward_noalloc(4, 4, 8, c, _abi.ADVECT_F16S, 16, 16, 16, 16, 16, 16, s)
+        assert e.value.status == 1 and "power of two" in str(e.value)

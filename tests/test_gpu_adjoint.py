@@ -86,21 +86,68 @@ def test_autograd_backward_is_the_adjoint():
         assert torch.equal(t.grad, r)
 
 
+def _dyadic_coeffs(nz, seed):
+    """Coefficients that are powers of two (unit spacings, power-of-two
+    densities): with small-integer fields every operation of the forward and
+    the adjoint, in any of the three arithmetics, is exact."""
+    z = np.arange(nz, dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    rho = 2.0 ** (-rng.integers(0, 3, nz)).astype(np.float64)
+    rhon = 2.0 ** (-rng.integers(0, 3, nz)).astype(np.float64)
+    return workload.custom_grid(z, z - 0.5, rho, rhon, 1.0, 2.0)
+
+
+def _fsum_dot(a_list, b_list):
+    """sum_f <a_f, b_f> in binary64: per-plane partial sums on the device,
+    then a correctly rounded sum of the partials (math.fsum)."""
+    import math
+    parts = []
+    for a, b in zip(a_list, b_list):
+        parts.extend(torch.sum(a.to(torch.float64) * b.to(torch.float64), dim=(1, 2)).tolist())
+    return math.fsum(parts)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f64ff"])
+def test_dot_product_identity_exact_on_gpu(dtype):
+    """<J d, l> = <d, J^T l> with equality: J d is the exact tangent
+    F(x + d) - F(x) - F(d) of the quadratic map, formed from three library
+    forwards; on small-integer inputs with power-of-two coefficients nothing
+    rounds, so both sides are the same rational number (several tiles in y
+    and x, a ragged tail)."""
+    shape = (70, 44, 64)
+    grid = _dyadic_coeffs(shape[2], 51)
+    op, _ = make_op(shape, dtype, grid=grid)
+    tdt = op.torch_dtype
+    ints = lambda base: [dev(workload.small_int_field(shape, -3, 3, 52, base + f), tdt) for f in range(3)]  # noqa: E731
+    x, d, lam = ints(0), ints(3), ints(6)
+    fx = op.forward(*x)
+    fd = op.forward(*d)
+    fxd = op.forward(*(a + b for a, b in zip(x, d)))
+    jd = [a.double() - b.double() - c.double() for a, b, c in zip(fxd, fx, fd)]
+    jt = op.adjoint(*x, *lam)
+    lhs = _fsum_dot(jd, lam)
+    rhs = _fsum_dot(d, jt)
+    assert lhs != 0.0
+    assert lhs == rhs, (lhs, rhs, op.kernel_name(True))
+
+
 def test_dot_product_identity_on_gpu():
+    """Random winds and directions at full scale: J d = (F(x + d) - F(x - d)) / 2
+    exactly for the quadratic map, so only rounding separates the two sides;
+    bound 1e-12 relative to sum |d * J^T l|."""
     shape = (32, 24, 64)
     op, _ = make_op(shape, "f64")
     x = [dev(a) for a in workload.winds(*shape, seed=28)]
     d = [dev(a) for a in workload.cotangents(*shape, seed=29)]
     lam = [dev(a) for a in workload.cotangents(*shape, seed=30)]
-    h = 2.0 ** -10
-    fp = op.forward(*(a + h * b for a, b in zip(x, d)))
-    fm = op.forward(*(a - h * b for a, b in zip(x, d)))
-    jd = [(a - b) / (2 * h) for a, b in zip(fp, fm)]
+    fp = op.forward(*(a + b for a, b in zip(x, d)))
+    fm = op.forward(*(a - b for a, b in zip(x, d)))
+    jd = [(a - b) * 0.5 for a, b in zip(fp, fm)]
     jt = op.adjoint(*x, *lam)
-    lhs = sum(torch.sum(a * b).item() for a, b in zip(jd, lam))
-    rhs = sum(torch.sum(a * b).item() for a, b in zip(d, jt))
-    mag = sum(torch.sum(torch.abs(a * b)).item() for a, b in zip(d, jt))
-    assert abs(lhs - rhs) <= 1e-12 * mag * 1e3
+    lhs = _fsum_dot(jd, lam)
+    rhs = _fsum_dot(d, jt)
+    mag = _fsum_dot([a.abs() for a in d], [b.abs() for b in jt])
+    assert abs(lhs - rhs) <= 1e-12 * mag, (lhs, rhs, mag)
 
 
 def test_central_differences_at_probe_points():

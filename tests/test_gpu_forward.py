@@ -141,3 +141,18 @@ def test_forward_rejects_aliasing_and_wrong_device_memory():
         _abi.advect_forward(op.handle, u.data_ptr() + 4, v.data_ptr(), w.data_ptr(),
                             *(t.data_ptr() for t in out))
     assert "aligned" in str(e.value)
+
+
+def test_forward_f16s_rejects_scales_that_are_not_powers_of_two():
+    from paper_2010_01545_gb300 import AdvectError
+    shape = (8, 8, 8)
+    op, _ = make_op(shape, "f16s")
+    h = [torch.zeros(shape, dtype=torch.float16, device="cuda") for _ in range(3)]
+    good = [16.0, 16.0, 8.0] + op.output_scales([16.0, 16.0, 8.0])
+    op.forward(*h, scales=good)
+    for q, bad in ((0, 12.0), (2, 0.3), (5, 48.0)):
+        s = list(good)
+        s[q] = bad
+        with pytest.raises(AdvectError) as e:
+            op.forward(*h, scales=s)
+        assert e.value.status == 1 and "power of two" in str(e.value)

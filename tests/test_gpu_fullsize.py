@@ -47,6 +47,16 @@ def device_normal(shape, seed, n=3, dtype=torch.float64):
     return [torch.randn(shape, generator=gen, device="cuda", dtype=torch.float64).to(dtype) for _ in range(n)]
 
 
+def fsum_dot(a_list, b_list):
+    """sum_f <a_f, b_f> in binary64: per-plane partial sums on the device,
+    then a correctly rounded sum of the partials (math.fsum)."""
+    import math
+    parts = []
+    for a, b in zip(a_list, b_list):
+        parts.extend(torch.sum(a.to(torch.float64) * b.to(torch.float64), dim=(1, 2)).tolist())
+    return math.fsum(parts)
+
+
 def sample_columns(shape, n_random, seed):
     """Random columns plus every boundary class of the periodic grid."""
     nx, ny, _ = shape
@@ -228,16 +238,18 @@ def test_adjoint_f64_1024x1024x128_dot_product_and_probes():
     x = device_winds(shape, 41)
     d = device_normal(shape, 42)
     lam = device_normal(shape, 43)
-    h = 2.0 ** -10
-    fp = op.forward(*(a + h * b for a, b in zip(x, d)))
-    fm = op.forward(*(a - h * b for a, b in zip(x, d)))
-    jd = [(a - b) / (2 * h) for a, b in zip(fp, fm)]
+    # the map is quadratic: J d = (F(x + d) - F(x - d)) / 2 exactly, with a
+    # full-scale direction so that only the rounding of the two forwards
+    # (relative ~1e-16) separates the two sides
+    fp = op.forward(*(a + b for a, b in zip(x, d)))
+    fm = op.forward(*(a - b for a, b in zip(x, d)))
+    jd = [(a - b) * 0.5 for a, b in zip(fp, fm)]
     del fp, fm
     jt = op.adjoint(*x, *lam)
-    lhs = sum(torch.sum(a * b).item() for a, b in zip(jd, lam))
-    rhs = sum(torch.sum(a * b).item() for a, b in zip(d, jt))
-    mag = sum(torch.sum(torch.abs(a * b)).item() for a, b in zip(d, jt))
-    assert abs(lhs - rhs) <= 1e-10 * mag
+    lhs = fsum_dot(jd, lam)
+    rhs = fsum_dot(d, jt)
+    mag = fsum_dot([a.abs() for a in d], [b.abs() for b in jt])
+    assert abs(lhs - rhs) <= 1e-12 * mag, (lhs, rhs, mag)
     del jd, d
     rng = np.random.default_rng(44)
     eps = 1e-6
