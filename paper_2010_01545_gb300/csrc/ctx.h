@@ -77,13 +77,6 @@ SweepCfg default_sweep(int nz, int elem);  // ty == 0: the shape cannot use the 
 // The forward tile a new context of this element type (Dtype) starts from,
 // before the tuning cache or an environment override.
 SweepCfg default_fwd_sweep(int nz, int dtype);
-// A sweep launch is (ceil(ny / ty), ceil(planes / lx)) CTAs and gridDim.y is
-// at most 65535, so an x extent longer than 65535 tiles takes longer tiles.
-inline SweepCfg fit_planes(SweepCfg c, int planes) {
-  const int need = (int)(((long long)planes + 65534) / 65535);
-  if (c.lx < need) c.lx = need;
-  return c;
-}
 cudaError_t tune_single(advect_ctx& ctx, int adj, const FwdArgs* fa, const AdjArgs* aa, cudaStream_t st);
 cudaError_t launch_fwd(const advect_ctx& ctx, const FwdArgs& a, cudaStream_t st);
 cudaError_t launch_adj(const advect_ctx& ctx, const AdjArgs& a, cudaStream_t st);

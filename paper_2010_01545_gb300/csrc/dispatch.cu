@@ -26,9 +26,11 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 // Default plane-sweep tile for a column height and element size; ty = 0 when
 // the sweep kernel cannot take this shape.
-SweepCfg default_sweep(int nz, int elem) {
+SweepCfg default_sweep(int nz, int elem) { return default_sweep_vec(nz, elem, sweep_vec(elem)); }
+
+// The same for vectors of P levels per thread.
+SweepCfg default_sweep_vec(int nz, int elem, int P) {
   SweepCfg c{0, 64, 4, 1};
-  const int P = sweep_vec(elem);
   if (nz % P || (nz * elem) % 16) return c;
   const int kb = nz / P;
   if (kb > 256) return c;

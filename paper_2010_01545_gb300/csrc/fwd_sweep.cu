@@ -8,7 +8,8 @@ size_t sweep_smem_bytes(int nz, int elem, const SweepCfg& cfg) {
   return sweep::ring_bytes(cfg.nb, (size_t)3 * (cfg.ty + 2) * nz * elem);
 }
 
-int sweep_vec(int elem) { return elem == 8 ? 2 : 4; }
+// levels per thread of the forward sweep: binary64 2, binary32 4, binary16 8
+int sweep_vec(int elem) { return elem == 8 ? 2 : (elem == 4 ? 4 : 8); }
 
 cudaError_t launch_fwd_sweep(int dtype, const FwdArgs& a, const SweepCfg& cfg, int* flag, cudaStream_t st) {
   if (a.i1 <= a.i0) return cudaSuccess;

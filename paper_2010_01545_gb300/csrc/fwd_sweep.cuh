@@ -10,7 +10,10 @@
 // (sweep_core.cuh).
 #pragma once
 
+#include <type_traits>
+
 #include "sweep_core.cuh"
+#include "sweep_h16.cuh"
 
 namespace advect {
 namespace {  // internal linkage: each translation unit keeps its own kernels
@@ -57,6 +60,56 @@ __global__ void __launch_bounds__(OCC == 1 ? 256 : 128, OCC) fwd_sweep_kernel(Sw
   sweep::forward_tile<T, F64Z, SPLIT, INTEG>(t, R, p.flag);
 }
 
+// F16S source terms without binary64 levels: the 8-level sweep of
+// sweep_h16.cuh (p.kb = nz / 8).
+template <int OCC, bool SPLIT>
+__global__ void __launch_bounds__(OCC == 1 ? 256 : 128, OCC) fwd_h16_kernel(SweepParams p) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const sweep::Ring R = sweep::make_ring(smem_raw, p.nb, p.slot_cap);
+  sweep::Tile<__half> t;
+  t.f[0] = (const __half*)p.a.u;
+  t.f[1] = (const __half*)p.a.v;
+  t.f[2] = (const __half*)p.a.w;
+  t.nf = 3;
+  t.o[0] = (__half*)p.a.su;
+  t.o[1] = (__half*)p.a.sv;
+  t.o[2] = (__half*)p.a.sw;
+  t.nx = p.a.s.nx;
+  t.ny = p.a.s.ny;
+  t.nz = p.a.s.nz;
+  t.j0 = blockIdx.x * p.ty;
+  t.ty = p.ty;
+  t.kb = p.kb;
+  t.i_lo = p.a.i0 + blockIdx.y * p.lx;
+  t.i_hi = min(t.i_lo + p.lx, p.a.i1);
+  t.c = p.a.c;
+  t.sc = p.a.sc;
+  t.f64_levels = 0;
+  t.wait_budget = p.a.wait_budget;
+  t.skip_plane = p.a.skip_plane;
+  sweep::forward_tile_h16<SPLIT>(t, R, p.flag);
+}
+
+template <int OCC, bool SPLIT>
+cudaError_t launch_h16_v(const SweepParams& p, dim3 grid, int threads, size_t smem, cudaStream_t st) {
+  if (threads > (OCC == 1 ? 256 : 128)) return cudaErrorInvalidConfiguration;
+  static int attr_bytes = -1;
+  if ((int)smem > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(fwd_h16_kernel<OCC, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_bytes = (int)smem;
+  }
+  fwd_h16_kernel<OCC, SPLIT><<<grid, threads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int OCC>
+cudaError_t launch_h16_occ(const SweepParams& p, dim3 grid, int threads, size_t smem, cudaStream_t st) {
+  if (32 % p.kb != 0) return launch_h16_v<OCC, true>(p, grid, threads, smem, st);
+  return launch_h16_v<OCC, false>(p, grid, threads, smem, st);
+}
+
 template <typename T, int OCC, bool F64Z, bool SPLIT, bool INTEG>
 cudaError_t launch_v(const SweepParams& p, dim3 grid, int threads, size_t smem, cudaStream_t st) {
   if (threads > (OCC == 1 ? 256 : 128)) return cudaErrorInvalidConfiguration;
@@ -85,8 +138,34 @@ cudaError_t launch_f64z(const SweepParams& p, dim3 grid, int threads, size_t sme
 }
 
 template <typename T, bool INTEG>
-cudaError_t launch_t(const FwdArgs& a, const SweepCfg& cfg, int* flag, cudaStream_t st) {
+cudaError_t launch_t(const FwdArgs& a, const SweepCfg& cfg_in, int* flag, cudaStream_t st) {
   constexpr int P = sweep::VecIO<T>::P;
+  SweepCfg cfg = cfg_in;
+  if constexpr (std::is_same<T, __half>::value) {
+    if (!INTEG && a.f64_levels == 0) {
+      // the 8-level F16S sweep, tile as given
+      SweepParams p;
+      p.a = a;
+      p.ty = cfg.ty;
+      p.kb = a.s.nz / sweep::h16::P;
+      p.lx = cfg.lx;
+      p.nb = cfg.nb;
+      p.slot_cap = (size_t)3 * (cfg.ty + 2) * a.s.nz * sizeof(__half);
+      p.flag = flag;
+      const size_t smem = sweep_smem_bytes(a.s.nz, (int)sizeof(__half), cfg);
+      const dim3 grid((a.s.ny + cfg.ty - 1) / cfg.ty, (a.i1 - a.i0 + cfg.lx - 1) / cfg.lx);
+      const int threads = cfg.ty * p.kb;
+      switch (cfg.occ) {
+        case 3: return launch_h16_occ<3>(p, grid, threads, smem, st);
+        case 4: return launch_h16_occ<4>(p, grid, threads, smem, st);
+        default: return launch_h16_occ<1>(p, grid, threads, smem, st);
+      }
+    }
+    // the integration epilogue and the binary64 near-surface levels run the
+    // generic sweep with 4-level binary16 vectors: its own default tile
+    cfg = fit_planes(default_sweep_vec(a.s.nz, (int)sizeof(__half), P), a.i1 - a.i0);
+    if (cfg.ty == 0) return launch_fwd_point(kF16S, a, st);
+  }
   SweepParams p;
   p.a = a;
   p.ty = cfg.ty;

@@ -54,6 +54,15 @@ cudaError_t launch_adj_point(int dtype, const AdjArgs& a, cudaStream_t st);
 // aligned fields, ty * nz / sweep_vec(elem) a multiple of 32 and <= 256.
 int sweep_vec(int elem);
 size_t sweep_smem_bytes(int nz, int elem, const SweepCfg& cfg);
+// Default tile for vectors of vec levels per thread (ty == 0: not sweepable).
+SweepCfg default_sweep_vec(int nz, int elem, int vec);
+// A sweep launch is (ceil(ny / ty), ceil(planes / lx)) CTAs and gridDim.y is
+// at most 65535, so an x extent longer than 65535 tiles takes longer tiles.
+inline SweepCfg fit_planes(SweepCfg c, int planes) {
+  const int need = (int)(((long long)planes + 65534) / 65535);
+  if (c.lx < need) c.lx = need;
+  return c;
+}
 cudaError_t launch_fwd_sweep(int dtype, const FwdArgs& a, const SweepCfg& cfg, int* flag, cudaStream_t st);
 // The same sweep with the integration epilogue (a.integ != 0; fwd_integ.cu).
 cudaError_t launch_fwd_sweep_integ(int dtype, const FwdArgs& a, const SweepCfg& cfg, int* flag,
