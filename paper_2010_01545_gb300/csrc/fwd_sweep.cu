@@ -5,7 +5,9 @@
 namespace advect {
 
 size_t sweep_smem_bytes(int nz, int elem, const SweepCfg& cfg) {
-  return sweep::ring_bytes(cfg.nb, (size_t)3 * (cfg.ty + 2) * nz * elem);
+  // the F16S sweep keeps its coefficient table after the ring
+  return sweep::ring_bytes(cfg.nb, (size_t)3 * (cfg.ty + 2) * nz * elem) +
+         (elem == 2 ? sweep::h16::table_bytes(nz) : 0);
 }
 
 // levels per thread of the forward sweep: binary64 2, binary32 4, binary16 8

@@ -89,13 +89,28 @@ __device__ __forceinline__ uint32_t pack_h2(float2 v) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// Per-thread constants of the sweep (pairs for levels (q, q+1)).
+// Per-thread constants of the sweep (pairs for levels (q, q+1)).  The
+// per-level coefficients are read from a shared-memory table each plane
+// (registers are the scarce resource at four CTAs per SM).  For the level
+// pair (k, k+1), k = 8 kb + 2 qp, the table holds (tzc1, tzc1, -tzc2, -tzc2)
+// of levels (k, k+1, k, k+1) at entry qp * KB + kb of its first half and
+// (tzd1, tzd1, -tzd2, -tzd2) at the same entry of its second half, so the
+// k-blocks of a row read consecutive 16-byte entries (no bank conflicts).
 struct Consts {
   float2 tcx, ntcx, tcy, ntcy;  // folded horizontal coefficients and negations
-  float2 c1[4], nc2[4];         // tzc1, -tzc2 of the thread's levels (u and v)
-  float2 d1[4], nd2[4];         // tzd1, -tzd2 (w)
   float2 o[3];                  // output factors of su, sv, sw
+  uint32_t tab;                 // shared-memory address of the thread's entry for qp = 0
+  uint32_t qstride, half;       // bytes between qp entries, and to the tzd half
 };
+
+// Shared-memory bytes of the coefficient table of an nz-level column.
+__host__ __device__ inline size_t table_bytes(int nz) { return (size_t)(nz / 2) * 2 * sizeof(float4); }
+
+__device__ __forceinline__ float4 lds128(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
+}
 
 // The vectors a plane's arithmetic reads (see the file comment of
 // sweep_core.cuh for the names: X = plane offset, Y = row offset).
@@ -109,6 +124,10 @@ struct Plane {
 template <int Q>
 __device__ __forceinline__ void level_pair(const Plane& p, const Consts& k, uint32_t& ou, uint32_t& ov,
                                            uint32_t& ow) {
+  const uint32_t a = k.tab + (Q / 2) * k.qstride;
+  const float4 zc = lds128(a), zd = lds128(a + k.half);
+  const float2 c1 = make_float2(zc.x, zc.y), nc2 = make_float2(zc.z, zc.w);
+  const float2 d1 = make_float2(zd.x, zd.y), nd2 = make_float2(zd.z, zd.w);
   float2 A, B, C, D, L, H;
   // su (Listing 1): x faces, y faces, lower and upper vertical faces
   A.x = mf<Q, Q>(p.UXM, p.UXM, mf<Q, Q>(p.UXM, p.U0, 0.f));
@@ -127,8 +146,8 @@ __device__ __forceinline__ void level_pair(const Plane& p, const Consts& k, uint
   h = f2fma(k.ntcx, B, h);
   h = f2fma(k.tcy, C, h);
   h = f2fma(k.ntcy, D, h);
-  h = f2fma(k.c1[Q / 2], L, h);
-  h = f2fma(k.nc2[Q / 2], H, h);
+  h = f2fma(c1, L, h);
+  h = f2fma(nc2, H, h);
   ou = pack_h2(f2mul(k.o[0], h));
   // sv
   A.x = mf<Q, Q>(p.VXM, p.UXM, mf<Q, Q>(p.VXM, p.UXMYP, 0.f));
@@ -147,8 +166,8 @@ __device__ __forceinline__ void level_pair(const Plane& p, const Consts& k, uint
   h = f2fma(k.ntcx, B, h);
   h = f2fma(k.tcy, C, h);
   h = f2fma(k.ntcy, D, h);
-  h = f2fma(k.c1[Q / 2], L, h);
-  h = f2fma(k.nc2[Q / 2], H, h);
+  h = f2fma(c1, L, h);
+  h = f2fma(nc2, H, h);
   ov = pack_h2(f2mul(k.o[1], h));
   // sw
   A.x = mf<Q, Q>(p.WXM, p.UXM, mf<Q, Q + 1>(p.WXM, p.UXM, 0.f));
@@ -167,8 +186,8 @@ __device__ __forceinline__ void level_pair(const Plane& p, const Consts& k, uint
   h = f2fma(k.ntcx, B, h);
   h = f2fma(k.tcy, C, h);
   h = f2fma(k.ntcy, D, h);
-  h = f2fma(k.d1[Q / 2], L, h);
-  h = f2fma(k.nd2[Q / 2], H, h);
+  h = f2fma(d1, L, h);
+  h = f2fma(nd2, H, h);
   ow = pack_h2(f2mul(k.o[2], h));
 }
 
@@ -210,6 +229,16 @@ __device__ bool forward_tile_h16(const Tile<__half>& t, const Ring& R, int* flag
   const int nplanes = t.i_hi - t.i_lo + 2;
   const int rows = t.ty + 2;
 
+  // coefficient table after the ring (ordered before use by start_tile's
+  // barrier)
+  float4* tab = reinterpret_cast<float4*>(R.slots + ring_bytes(R.nb, R.slot_cap));
+  for (int pq = tid; pq < nz / 2; pq += blockDim.x) {
+    const float* f = t.c.f;
+    const int k = 2 * pq, e = (pq % 4) * KB + pq / 4;
+    tab[e] = make_float4(f[TZC1 * nz + k], f[TZC1 * nz + k + 1], -f[TZC2 * nz + k], -f[TZC2 * nz + k + 1]);
+    tab[nz / 2 + e] =
+        make_float4(f[TZD1 * nz + k], f[TZD1 * nz + k + 1], -f[TZD2 * nz + k], -f[TZD2 * nz + k + 1]);
+  }
   start_tile<3>(t, R, nplanes);
   bool ok = true;
   if (tid < active_threads) {
@@ -218,6 +247,9 @@ __device__ bool forward_tile_h16(const Tile<__half>& t, const Ring& R, int* flag
     const int j = t.j0 + rr;
     const bool row_ok = j < ny;
     Consts K;
+    K.tab = smem_addr(tab + kb);
+    K.qstride = (uint32_t)(KB * sizeof(float4));
+    K.half = (uint32_t)(nz / 2 * sizeof(float4));
     {
       const float s_u = t.sc.in[0], s_v = t.sc.in[1], s_w = t.sc.in[2];
       const float iw = 1.f / s_w;
@@ -231,15 +263,6 @@ __device__ bool forward_tile_h16(const Tile<__half>& t, const Ring& R, int* flag
       K.o[0] = make_float2(ou, ou);
       K.o[1] = make_float2(ov, ov);
       K.o[2] = make_float2(ow, ow);
-      const float* f = t.c.f;
-#pragma unroll
-      for (int q = 0; q < P / 2; ++q) {
-        const int k = k0 + 2 * q;
-        K.c1[q] = make_float2(__ldg(f + TZC1 * nz + k), __ldg(f + TZC1 * nz + k + 1));
-        K.nc2[q] = make_float2(-__ldg(f + TZC2 * nz + k), -__ldg(f + TZC2 * nz + k + 1));
-        K.d1[q] = make_float2(__ldg(f + TZD1 * nz + k), __ldg(f + TZD1 * nz + k + 1));
-        K.nd2[q] = make_float2(-__ldg(f + TZD2 * nz + k), -__ldg(f + TZD2 * nz + k + 1));
-      }
     }
     // su, sv (level 0) and sw (levels 0 and nz-1) are zero: masks on the
     // packed results of the first and last level pair
