@@ -9,9 +9,10 @@
 // addend and result: the product of two binary16 numbers is exact in
 // binary32).  The stored halves are never converted: they stay packed two
 // to a register, and the multiply-add takes its operands from either half.
-// The four partial sums of a field (x-faces in, out; y-faces in, out) and
-// the two vertical products are combined with the direction's coefficient by
-// two-wide binary32 multiply-adds on the levels (q, q+1) of a register pair.
+// Each horizontal direction's four products are one chain (the outflow
+// pair first, its sum entering the inflow pair's chain negated), and the x,
+// y and two vertical sums are combined with their coefficients by two-wide
+// binary32 multiply-adds on the levels (q, q+1) of a register pair.
 //
 // A thread owns 8 consecutive levels of one column (one 16-byte vector per
 // field and row).  The input scales are powers of two and are folded into
@@ -97,7 +98,7 @@ __device__ __forceinline__ uint32_t pack_h2(float2 v) {
 // (tzd1, tzd1, -tzd2, -tzd2) at the same entry of its second half, so the
 // k-blocks of a row read consecutive 16-byte entries (no bank conflicts).
 struct Consts {
-  float2 tcx, ntcx, tcy, ntcy;  // folded horizontal coefficients and negations
+  float2 tcx, tcy;  // folded horizontal coefficients
   float2 o[3];                  // output factors of su, sv, sw
   uint32_t tab;                 // shared-memory address of the thread's entry for qp = 0
   uint32_t qstride, half;       // bytes between qp entries, and to the tzd half
@@ -128,64 +129,54 @@ __device__ __forceinline__ void level_pair(const Plane& p, const Consts& k, uint
   const float4 zc = lds128(a), zd = lds128(a + k.half);
   const float2 c1 = make_float2(zc.x, zc.y), nc2 = make_float2(zc.z, zc.w);
   const float2 d1 = make_float2(zd.x, zd.y), nd2 = make_float2(zd.z, zd.w);
-  float2 A, B, C, D, L, H;
-  // su (Listing 1): x faces, y faces, lower and upper vertical faces
-  A.x = mf<Q, Q>(p.UXM, p.UXM, mf<Q, Q>(p.UXM, p.U0, 0.f));
-  A.y = mf<Q + 1, Q + 1>(p.UXM, p.UXM, mf<Q + 1, Q + 1>(p.UXM, p.U0, 0.f));
-  B.x = mf<Q, Q>(p.UXP, p.U0, mf<Q, Q>(p.UXP, p.UXP, 0.f));
-  B.y = mf<Q + 1, Q + 1>(p.UXP, p.U0, mf<Q + 1, Q + 1>(p.UXP, p.UXP, 0.f));
-  C.x = mf<Q, Q>(p.UYM, p.VYM, mf<Q, Q>(p.UYM, p.VXPYM, 0.f));
-  C.y = mf<Q + 1, Q + 1>(p.UYM, p.VYM, mf<Q + 1, Q + 1>(p.UYM, p.VXPYM, 0.f));
-  D.x = mf<Q, Q>(p.UYP, p.V0, mf<Q, Q>(p.UYP, p.VXP, 0.f));
-  D.y = mf<Q + 1, Q + 1>(p.UYP, p.V0, mf<Q + 1, Q + 1>(p.UYP, p.VXP, 0.f));
+  float2 X, Y, L, H;
+  // su (Listing 1): x faces in minus out, y faces in minus out (each a chain
+  // of four products ending in the inflow pair, the outflow pair's sum
+  // entering negated), lower and upper vertical faces
+  X.x = mf<Q, Q>(p.UXM, p.UXM, mf<Q, Q>(p.UXM, p.U0, -mf<Q, Q>(p.UXP, p.U0, mf<Q, Q>(p.UXP, p.UXP, 0.f))));
+  X.y = mf<Q + 1, Q + 1>(p.UXM, p.UXM,
+                         mf<Q + 1, Q + 1>(p.UXM, p.U0, -mf<Q + 1, Q + 1>(p.UXP, p.U0, mf<Q + 1, Q + 1>(p.UXP, p.UXP, 0.f))));
+  Y.x = mf<Q, Q>(p.UYM, p.VYM, mf<Q, Q>(p.UYM, p.VXPYM, -mf<Q, Q>(p.UYP, p.V0, mf<Q, Q>(p.UYP, p.VXP, 0.f))));
+  Y.y = mf<Q + 1, Q + 1>(p.UYM, p.VYM,
+                         mf<Q + 1, Q + 1>(p.UYM, p.VXPYM, -mf<Q + 1, Q + 1>(p.UYP, p.V0, mf<Q + 1, Q + 1>(p.UYP, p.VXP, 0.f))));
   L.x = mf<Q - 1, Q - 1>(p.U0, p.W0, mf<Q - 1, Q - 1>(p.U0, p.WXP, 0.f));
   L.y = mf<Q, Q>(p.U0, p.W0, mf<Q, Q>(p.U0, p.WXP, 0.f));
   H.x = mf<Q + 1, Q>(p.U0, p.W0, mf<Q + 1, Q>(p.U0, p.WXP, 0.f));
   H.y = mf<Q + 2, Q + 1>(p.U0, p.W0, mf<Q + 2, Q + 1>(p.U0, p.WXP, 0.f));
-  float2 h = f2mul(k.tcx, A);
-  h = f2fma(k.ntcx, B, h);
-  h = f2fma(k.tcy, C, h);
-  h = f2fma(k.ntcy, D, h);
+  float2 h = f2mul(k.tcx, X);
+  h = f2fma(k.tcy, Y, h);
   h = f2fma(c1, L, h);
   h = f2fma(nc2, H, h);
   ou = pack_h2(f2mul(k.o[0], h));
   // sv
-  A.x = mf<Q, Q>(p.VXM, p.UXM, mf<Q, Q>(p.VXM, p.UXMYP, 0.f));
-  A.y = mf<Q + 1, Q + 1>(p.VXM, p.UXM, mf<Q + 1, Q + 1>(p.VXM, p.UXMYP, 0.f));
-  B.x = mf<Q, Q>(p.VXP, p.U0, mf<Q, Q>(p.VXP, p.UYP, 0.f));
-  B.y = mf<Q + 1, Q + 1>(p.VXP, p.U0, mf<Q + 1, Q + 1>(p.VXP, p.UYP, 0.f));
-  C.x = mf<Q, Q>(p.VYM, p.V0, mf<Q, Q>(p.VYM, p.VYM, 0.f));
-  C.y = mf<Q + 1, Q + 1>(p.VYM, p.V0, mf<Q + 1, Q + 1>(p.VYM, p.VYM, 0.f));
-  D.x = mf<Q, Q>(p.VYP, p.V0, mf<Q, Q>(p.VYP, p.VYP, 0.f));
-  D.y = mf<Q + 1, Q + 1>(p.VYP, p.V0, mf<Q + 1, Q + 1>(p.VYP, p.VYP, 0.f));
+  X.x = mf<Q, Q>(p.VXM, p.UXM, mf<Q, Q>(p.VXM, p.UXMYP, -mf<Q, Q>(p.VXP, p.U0, mf<Q, Q>(p.VXP, p.UYP, 0.f))));
+  X.y = mf<Q + 1, Q + 1>(p.VXM, p.UXM,
+                         mf<Q + 1, Q + 1>(p.VXM, p.UXMYP, -mf<Q + 1, Q + 1>(p.VXP, p.U0, mf<Q + 1, Q + 1>(p.VXP, p.UYP, 0.f))));
+  Y.x = mf<Q, Q>(p.VYM, p.V0, mf<Q, Q>(p.VYM, p.VYM, -mf<Q, Q>(p.VYP, p.V0, mf<Q, Q>(p.VYP, p.VYP, 0.f))));
+  Y.y = mf<Q + 1, Q + 1>(p.VYM, p.V0,
+                         mf<Q + 1, Q + 1>(p.VYM, p.VYM, -mf<Q + 1, Q + 1>(p.VYP, p.V0, mf<Q + 1, Q + 1>(p.VYP, p.VYP, 0.f))));
   L.x = mf<Q - 1, Q - 1>(p.V0, p.W0, mf<Q - 1, Q - 1>(p.V0, p.WYP, 0.f));
   L.y = mf<Q, Q>(p.V0, p.W0, mf<Q, Q>(p.V0, p.WYP, 0.f));
   H.x = mf<Q + 1, Q>(p.V0, p.W0, mf<Q + 1, Q>(p.V0, p.WYP, 0.f));
   H.y = mf<Q + 2, Q + 1>(p.V0, p.W0, mf<Q + 2, Q + 1>(p.V0, p.WYP, 0.f));
-  h = f2mul(k.tcx, A);
-  h = f2fma(k.ntcx, B, h);
-  h = f2fma(k.tcy, C, h);
-  h = f2fma(k.ntcy, D, h);
+  h = f2mul(k.tcx, X);
+  h = f2fma(k.tcy, Y, h);
   h = f2fma(c1, L, h);
   h = f2fma(nc2, H, h);
   ov = pack_h2(f2mul(k.o[1], h));
   // sw
-  A.x = mf<Q, Q>(p.WXM, p.UXM, mf<Q, Q + 1>(p.WXM, p.UXM, 0.f));
-  A.y = mf<Q + 1, Q + 1>(p.WXM, p.UXM, mf<Q + 1, Q + 2>(p.WXM, p.UXM, 0.f));
-  B.x = mf<Q, Q>(p.WXP, p.U0, mf<Q, Q + 1>(p.WXP, p.U0, 0.f));
-  B.y = mf<Q + 1, Q + 1>(p.WXP, p.U0, mf<Q + 1, Q + 2>(p.WXP, p.U0, 0.f));
-  C.x = mf<Q, Q>(p.WYM, p.VYM, mf<Q, Q + 1>(p.WYM, p.VYM, 0.f));
-  C.y = mf<Q + 1, Q + 1>(p.WYM, p.VYM, mf<Q + 1, Q + 2>(p.WYM, p.VYM, 0.f));
-  D.x = mf<Q, Q>(p.WYP, p.V0, mf<Q, Q + 1>(p.WYP, p.V0, 0.f));
-  D.y = mf<Q + 1, Q + 1>(p.WYP, p.V0, mf<Q + 1, Q + 2>(p.WYP, p.V0, 0.f));
+  X.x = mf<Q, Q>(p.WXM, p.UXM, mf<Q, Q + 1>(p.WXM, p.UXM, -mf<Q, Q>(p.WXP, p.U0, mf<Q, Q + 1>(p.WXP, p.U0, 0.f))));
+  X.y = mf<Q + 1, Q + 1>(p.WXM, p.UXM,
+                         mf<Q + 1, Q + 2>(p.WXM, p.UXM, -mf<Q + 1, Q + 1>(p.WXP, p.U0, mf<Q + 1, Q + 2>(p.WXP, p.U0, 0.f))));
+  Y.x = mf<Q, Q>(p.WYM, p.VYM, mf<Q, Q + 1>(p.WYM, p.VYM, -mf<Q, Q>(p.WYP, p.V0, mf<Q, Q + 1>(p.WYP, p.V0, 0.f))));
+  Y.y = mf<Q + 1, Q + 1>(p.WYM, p.VYM,
+                         mf<Q + 1, Q + 2>(p.WYM, p.VYM, -mf<Q + 1, Q + 1>(p.WYP, p.V0, mf<Q + 1, Q + 2>(p.WYP, p.V0, 0.f))));
   L.x = mf<Q - 1, Q>(p.W0, p.W0, mf<Q - 1, Q - 1>(p.W0, p.W0, 0.f));
   L.y = mf<Q, Q + 1>(p.W0, p.W0, mf<Q, Q>(p.W0, p.W0, 0.f));
   H.x = mf<Q + 1, Q>(p.W0, p.W0, mf<Q + 1, Q + 1>(p.W0, p.W0, 0.f));
   H.y = mf<Q + 2, Q + 1>(p.W0, p.W0, mf<Q + 2, Q + 2>(p.W0, p.W0, 0.f));
-  h = f2mul(k.tcx, A);
-  h = f2fma(k.ntcx, B, h);
-  h = f2fma(k.tcy, C, h);
-  h = f2fma(k.ntcy, D, h);
+  h = f2mul(k.tcx, X);
+  h = f2fma(k.tcy, Y, h);
   h = f2fma(d1, L, h);
   h = f2fma(nd2, H, h);
   ow = pack_h2(f2mul(k.o[2], h));
@@ -255,9 +246,7 @@ __device__ bool forward_tile_h16(const Tile<__half>& t, const Ring& R, int* flag
       const float iw = 1.f / s_w;
       const float tx = t.c.tcx_f * s_u * iw, ty = t.c.tcy_f * s_v * iw;
       K.tcx = make_float2(tx, tx);
-      K.ntcx = make_float2(-tx, -tx);
       K.tcy = make_float2(ty, ty);
-      K.ntcy = make_float2(-ty, -ty);
       const float ou = t.sc.inv_out[0] * s_u * s_w, ov = t.sc.inv_out[1] * s_v * s_w,
                   ow = t.sc.inv_out[2] * s_w * s_w;
       K.o[0] = make_float2(ou, ou);
