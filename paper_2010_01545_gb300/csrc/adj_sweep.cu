@@ -1,5 +1,7 @@
 // adj_sweep.cu -- single-grid plane-sweep adjoint: one tile per CTA.
-#include "adj_core.cuh"
+#include <type_traits>
+
+#include "adj_f32.cuh"
 
 namespace advect {
 namespace {
@@ -43,7 +45,10 @@ __global__ void __launch_bounds__(OCC == 1 ? 256 : 128, OCC) adj_sweep_kernel(Ad
   t.f64_levels = 0;
   t.wait_budget = p.a.wait_budget;
   t.skip_plane = p.a.skip_plane;
-  sweep::adjoint_tile<T, SPLIT>(t, R, p.flag);
+  if constexpr (std::is_same<T, float>::value)
+    sweep::adjoint_tile_f32v4<SPLIT>(t, R, p.flag);  // 4 levels per thread
+  else
+    sweep::adjoint_tile<T, SPLIT>(t, R, p.flag);
 }
 
 template <typename T, int OCC, bool SPLIT>
@@ -71,7 +76,7 @@ cudaError_t launch_t(const AdjArgs& a, const SweepCfg& cfg, int* flag, cudaStrea
   AdjParams p;
   p.a = a;
   p.ty = cfg.ty;
-  p.kb = a.s.nz / sweep::AdjIO<T>::P;
+  p.kb = a.s.nz / adj_sweep_vec((int)sizeof(T));
   p.lx = cfg.lx;
   p.nb = cfg.nb;
   p.slot_cap = (size_t)6 * (cfg.ty + 2) * a.s.nz * sizeof(T);
@@ -89,10 +94,13 @@ cudaError_t launch_t(const AdjArgs& a, const SweepCfg& cfg, int* flag, cudaStrea
 }  // namespace
 
 size_t adj_sweep_smem_bytes(int nz, int elem, const SweepCfg& cfg) {
-  return sweep::ring_bytes(cfg.nb, (size_t)6 * (cfg.ty + 2) * nz * elem);
+  // the binary32 sweep keeps its coefficient table after the ring
+  return sweep::ring_bytes(cfg.nb, (size_t)6 * (cfg.ty + 2) * nz * elem) +
+         (elem == 4 ? sweep::a4::table_bytes(nz) : 0);
 }
 
-int adj_sweep_vec(int elem) { return elem == 8 ? 1 : 2; }
+// levels per thread of the adjoint sweep: 8-byte types 1, binary32 4
+int adj_sweep_vec(int elem) { return elem == 8 ? 1 : 4; }
 
 cudaError_t launch_adj_sweep(int dtype, const AdjArgs& a, const SweepCfg& cfg, int* flag, cudaStream_t st) {
   switch (dtype) {

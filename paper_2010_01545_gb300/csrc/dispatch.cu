@@ -100,8 +100,13 @@ SweepCfg default_adj_sweep(int nz, int elem) {
   while (ty > 1 && (ty * kb) % 32) --ty;
   if ((ty * kb) % 32) return c;
   c.ty = ty;
-  c.occ = target == 256 ? 1 : (elem == 4 ? 4 : 3);
-  const size_t cap = c.occ == 4 ? 54 * 1024 : (c.occ == 3 ? 72 * 1024 : 100 * 1024);
+  // binary32 (4 levels per thread, adj_f32.cuh): code for <= 168 registers
+  // (167, no spills) and three CTAs per SM, whose rings and coefficient
+  // tables must then fit a third of the SM's shared memory (measured at
+  // 1024 x 1024 x 128: 136.4 Gpts/s; uncapped at two CTAs per SM 115.5;
+  // capped for four 128.6-register CTAs, spilling, 54)
+  c.occ = target == 256 ? 1 : 3;
+  const size_t cap = elem == 4 ? 75 * 1024 : (c.occ == 3 ? 72 * 1024 : 100 * 1024);
   c.nb = 8;
   while (c.nb > 4 && adj_sweep_smem_bytes(nz, elem, c) > cap) --c.nb;
   if (adj_sweep_smem_bytes(nz, elem, c) > 220 * 1024 || (uint64_t)6 * (c.ty + 2) * nz * elem >= (1u << 20))
