@@ -104,7 +104,7 @@ SweepCfg default_adj_sweep(int nz, int elem) {
   // (167, no spills) and three CTAs per SM, whose rings and coefficient
   // tables must then fit a third of the SM's shared memory (measured at
   // 1024 x 1024 x 128: 136.4 Gpts/s; uncapped at two CTAs per SM 115.5;
-  // capped for four 128.6-register CTAs, spilling, 54)
+  // capped at 128 registers for four CTAs, spilling, 54)
   c.occ = target == 256 ? 1 : 3;
   const size_t cap = elem == 4 ? 75 * 1024 : (c.occ == 3 ? 72 * 1024 : 100 * 1024);
   c.nb = 8;

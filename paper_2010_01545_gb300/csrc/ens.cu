@@ -6,8 +6,10 @@
 // as many CTAs as fit on the GPU at once; each CTA takes the next tile index
 // from a device counter (atomicAdd), decodes it against the member table and
 // sweeps the tile with the same code as the single-grid kernels
-// (sweep::forward_tile / sweep::adjoint_tile).  Tiles are ordered largest
-// member first, so the dynamic queue ends with small tiles.
+// (sweep::forward_tile; for the adjoint sweep::adjoint_tile, or
+// sweep::adjoint_tile_f32v4 with binary32, whose coefficient table after the
+// ring is refilled per tile and sized for the largest column).  Tiles are
+// ordered largest member first, so the dynamic queue ends with small tiles.
 //
 // The member table lives in device memory and is re-uploaded (on the
 // caller's stream) only when the buffer pointers change.  Counter reset and
@@ -25,8 +27,10 @@
 #include <string>
 #include <vector>
 
+#include <type_traits>
+
 #include "../../include/advect.h"
-#include "adj_core.cuh"
+#include "adj_f32.cuh"
 #include "ctx.h"
 #include "ens.h"
 
@@ -96,14 +100,20 @@ __global__ void __launch_bounds__(kEnsThreads, OCC) ens_kernel(EnsParams p) {
       t.sc.base[q] = 1.f;
     }
     t.f64_levels = 0;
-    const bool ok = ADJ ? sweep::adjoint_tile<T, SPLIT>(t, R, p.flag)
-                        : sweep::forward_tile<T, false, SPLIT>(t, R, p.flag);
+    bool ok;
+    if constexpr (ADJ && std::is_same<T, float>::value)
+      ok = sweep::adjoint_tile_f32v4<SPLIT>(t, R, p.flag);
+    else if constexpr (ADJ)
+      ok = sweep::adjoint_tile<T, SPLIT>(t, R, p.flag);
+    else
+      ok = sweep::forward_tile<T, false, SPLIT>(t, R, p.flag);
     if (!ok) break;  // uniform across the CTA
   }
 }
 
 template <typename T>
 int vec_of(bool adj) {
+  if (adj && std::is_same<T, float>::value) return sweep::a4::P;
   return adj ? sweep::AdjIO<T>::P : sweep::VecIO<T>::P;
 }
 
@@ -141,6 +151,7 @@ struct EnsDir {  // one direction (forward or adjoint)
   int n_tiles = 0;
   size_t slot_cap = 0;
   bool split = false;  // some member's rows straddle warps
+  size_t table = 0;    // shared-memory coefficient table after the ring
   EnsCfg cfg{64, 6, 4};
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
@@ -164,6 +175,7 @@ static void build_table(const advect_ctx& ctx, EnsState& st, int adj, const void
   std::vector<MemberDesc<T>> v(n);
   int tile = 0;
   size_t cap = 0;
+  int max_nz = 0;
   bool split = false;
   const int P = vec_of<T>(adj != 0);
   for (int r = 0; r < n; ++r) {
@@ -190,8 +202,10 @@ static void build_table(const advect_ctx& ctx, EnsState& st, int adj, const void
     d.c.tcy_f = (float)mm.tcy;
     cap = std::max(cap, (size_t)(adj ? 6 : 3) * (d.ty + 2) * mm.nz * sizeof(T));
     split = split || (32 % d.kb) != 0;
+    max_nz = std::max(max_nz, mm.nz);
   }
   D.split = split;
+  D.table = (adj && std::is_same<T, float>::value) ? sweep::a4::table_bytes(max_nz) : 0;
   D.n_tiles = tile;
   D.slot_cap = (cap + 127) / 128 * 128;
   D.host_desc.resize(v.size() * sizeof(MemberDesc<T>));
@@ -199,7 +213,7 @@ static void build_table(const advect_ctx& ctx, EnsState& st, int adj, const void
 }
 
 size_t ens_smem_bytes(const EnsState& st, int adj, const EnsCfg& cfg) {
-  return sweep::ring_bytes(cfg.nb, st.dir[adj].slot_cap);
+  return sweep::ring_bytes(cfg.nb, st.dir[adj].slot_cap) + st.dir[adj].table;
 }
 
 // Check that every member can run the ensemble sweep for this element type.
@@ -208,8 +222,7 @@ advect_status ens_check_members(const advect_ctx& ctx, std::string& why) {
   for (size_t m = 0; m < ctx.members.size(); ++m) {
     const int nz = ctx.members[m].nz;
     for (int adj = 0; adj < 2; ++adj) {
-      const int P = elem == 8 ? (adj ? sweep::AdjIO<double>::P : sweep::VecIO<double>::P)
-                              : (adj ? sweep::AdjIO<float>::P : sweep::VecIO<float>::P);
+      const int P = elem == 8 ? vec_of<double>(adj != 0) : vec_of<float>(adj != 0);
       if (nz % P || (nz * elem) % 16 || member_ty(nz / P) == 0) {
         why = "member " + std::to_string(m) + ": nz = " + std::to_string(nz) +
               " not supported by the ensemble kernels (need nz * element size a multiple of 16 and"

@@ -222,7 +222,9 @@ advect_status advect_ensemble_create(int n, const int* nx, const int* ny, const 
   ctx->ens = st;
   for (int adj = 0; adj < 2; ++adj) {
     EnsCfg& cfg = ens_cfg(*st, adj);
-    cfg = EnsCfg{64, 6, 4};
+    // the binary32 adjoint (4 levels per thread) is built for three CTAs
+    // per SM (167 registers) and its ring must then fit a third of the SM
+    cfg = (adj && dtype == ADVECT_F32) ? EnsCfg{64, 4, 3} : EnsCfg{64, 6, 4};
     std::string v;
     if (tune_cache_get(ens_key(*ctx, adj), v)) parse_ens_cfg(v, cfg);
   }
