@@ -183,20 +183,27 @@ __device__ __forceinline__ void level_pair(const Plane& p, const Consts& k, uint
 }
 
 // Vertical halos by warp shuffle: the register holding level -1 (high half)
-// or level 8 (low half) of the neighbouring lane's vector; zero beyond the
-// column; from shared memory where the row crosses a warp boundary (SPLIT).
+// or level 8 (low half) of the neighbouring lane's vector; from shared
+// memory where the row crosses a warp boundary (SPLIT).  Beyond the column
+// the value is some other column's level; it is zeroed only where it can
+// reach an output that is kept.  Level -1 is read only by the arithmetic of
+// level 0, whose su, sv and sw are all cleared bit for bit afterwards, so the
+// halo below is never zeroed; level nz is read only at level nz-1, where sw
+// is cleared but su and sv multiply it by tzc2(nz-1) = 0, so the halos above
+// of u and v are zeroed (a non-finite neighbour times zero would not be
+// zero) and those of the other vectors are not (ZERO).
 template <bool SPLIT>
 __device__ __forceinline__ uint32_t halo_lo(const Ext& v, const __half* row, int k0, int kb, int lane) {
   uint32_t r = __shfl_up_sync(0xffffffffu, v.e[4], 1);
   if (SPLIT && lane == 0 && kb > 0) r = *reinterpret_cast<const uint32_t*>(row + k0 - 2);
-  return kb == 0 ? 0u : r;
+  return r;
 }
 
-template <bool SPLIT>
+template <bool SPLIT, bool ZERO>
 __device__ __forceinline__ uint32_t halo_hi(const Ext& v, const __half* row, int k0, int kb, int KB, int lane) {
   uint32_t r = __shfl_down_sync(0xffffffffu, v.e[1], 1);
   if (SPLIT && lane == 31 && kb < KB - 1) r = *reinterpret_cast<const uint32_t*>(row + k0 + P);
-  return kb == KB - 1 ? 0u : r;
+  return (ZERO && kb == KB - 1) ? 0u : r;
 }
 
 __device__ __forceinline__ void copy_levels(Ext& d, const Ext& s) {
@@ -291,13 +298,13 @@ __device__ bool forward_tile_h16(const Tile<__half>& t, const Ring& R, int* flag
       ld8(P1 + o_w0, p.W0);
       // halos carried into the first plane (the others come with each plane)
       p.U0.e[0] = halo_lo<SPLIT>(p.U0, P1 + o_u0 - k0, k0, kb, lane);
-      p.U0.e[5] = halo_hi<SPLIT>(p.U0, P1 + o_u0 - k0, k0, kb, KB, lane);
-      p.UXM.e[5] = halo_hi<SPLIT>(p.UXM, P0 + o_u0 - k0, k0, kb, KB, lane);
+      p.U0.e[5] = halo_hi<SPLIT, true>(p.U0, P1 + o_u0 - k0, k0, kb, KB, lane);
+      p.UXM.e[5] = halo_hi<SPLIT, false>(p.UXM, P0 + o_u0 - k0, k0, kb, KB, lane);
       p.V0.e[0] = halo_lo<SPLIT>(p.V0, P1 + o_v0 - k0, k0, kb, lane);
-      p.V0.e[5] = halo_hi<SPLIT>(p.V0, P1 + o_v0 - k0, k0, kb, KB, lane);
-      p.VYM.e[5] = halo_hi<SPLIT>(p.VYM, P1 + o_vm - k0, k0, kb, KB, lane);
+      p.V0.e[5] = halo_hi<SPLIT, true>(p.V0, P1 + o_v0 - k0, k0, kb, KB, lane);
+      p.VYM.e[5] = halo_hi<SPLIT, false>(p.VYM, P1 + o_vm - k0, k0, kb, KB, lane);
       p.W0.e[0] = halo_lo<SPLIT>(p.W0, P1 + o_w0 - k0, k0, kb, lane);
-      p.W0.e[5] = halo_hi<SPLIT>(p.W0, P1 + o_w0 - k0, k0, kb, KB, lane);
+      p.W0.e[5] = halo_hi<SPLIT, false>(p.W0, P1 + o_w0 - k0, k0, kb, KB, lane);
     }
     release(0, q0);
     SlotPos pc = q1, pn = q1;
@@ -324,11 +331,11 @@ __device__ bool forward_tile_h16(const Tile<__half>& t, const Ring& R, int* flag
       p.WXP.e[0] = halo_lo<SPLIT>(p.WXP, Pn + o_w0 - k0, k0, kb, lane);
       p.WYP.e[0] = halo_lo<SPLIT>(p.WYP, Pc + o_wp - k0, k0, kb, lane);
       p.UXP.e[0] = halo_lo<SPLIT>(p.UXP, Pn + o_u0 - k0, k0, kb, lane);
-      p.UXP.e[5] = halo_hi<SPLIT>(p.UXP, Pn + o_u0 - k0, k0, kb, KB, lane);
+      p.UXP.e[5] = halo_hi<SPLIT, true>(p.UXP, Pn + o_u0 - k0, k0, kb, KB, lane);
       p.VXP.e[0] = halo_lo<SPLIT>(p.VXP, Pn + o_v0 - k0, k0, kb, lane);
-      p.VXP.e[5] = halo_hi<SPLIT>(p.VXP, Pn + o_v0 - k0, k0, kb, KB, lane);
-      p.VXPYM.e[5] = halo_hi<SPLIT>(p.VXPYM, Pn + o_vm - k0, k0, kb, KB, lane);
-      p.WXP.e[5] = halo_hi<SPLIT>(p.WXP, Pn + o_w0 - k0, k0, kb, KB, lane);
+      p.VXP.e[5] = halo_hi<SPLIT, true>(p.VXP, Pn + o_v0 - k0, k0, kb, KB, lane);
+      p.VXPYM.e[5] = halo_hi<SPLIT, false>(p.VXPYM, Pn + o_vm - k0, k0, kb, KB, lane);
+      p.WXP.e[5] = halo_hi<SPLIT, false>(p.WXP, Pn + o_w0 - k0, k0, kb, KB, lane);
       release(qc, pc);
       pc = pn;
       pn.next(NB);
