@@ -8,6 +8,7 @@
 #include "ctx.h"
 #include "ens.h"
 #include "sweep_core.cuh"
+#include "sweep_ff.cuh"
 #include "tune.h"
 
 #include <functional>
@@ -75,8 +76,9 @@ static void sweep_override(const char* var, SweepCfg& c, int nz, int elem, int v
   if (n == 3) o.occ = 1;
   const int kb = nz / vec;
   if (o.ty < 1 || o.lx < 1 || o.nb < 4 || o.ty * kb > 256 || (o.ty * kb) % 32) return;
-  if (o.occ != 1 && o.occ != 3 && o.occ != 4) return;
-  if (o.occ != 1 && o.ty * kb > 128) return;
+  if (o.occ < 1 || o.occ > 4) return;
+  if (o.occ > 2 && o.ty * kb > 128) return;
+  if (o.occ == 2 && o.ty * kb > 224) return;
   const size_t smem = sweep::ring_bytes(o.nb, (size_t)nf * (o.ty + 2) * nz * elem);
   if (smem > 220 * 1024 || (uint64_t)nf * (o.ty + 2) * nz * elem >= (1u << 20)) return;
   c = o;
@@ -147,8 +149,9 @@ bool parse_cfg(const std::string& v, int nz, int elem, int vec, int nf, int& kin
   if (nz % vec || (nz * elem) % 16) return false;
   const int kb = nz / vec;
   if (o.ty < 1 || o.lx < 1 || o.nb < 4 || o.ty * kb > 256 || (o.ty * kb) % 32) return false;
-  if (o.occ != 1 && o.occ != 3 && o.occ != 4) return false;
-  if (o.occ != 1 && o.ty * kb > 128) return false;
+  if (o.occ < 1 || o.occ > 4) return false;
+  if (o.occ > 2 && o.ty * kb > 128) return false;
+  if (o.occ == 2 && o.ty * kb > 224) return false;
   if (sweep::ring_bytes(o.nb, (size_t)nf * (o.ty + 2) * nz * elem) > 220 * 1024) return false;
   kind = 1;
   c = o;
@@ -156,14 +159,15 @@ bool parse_cfg(const std::string& v, int nz, int elem, int vec, int nf, int& kin
 }
 
 // Candidate tiles for a column height: 128-thread tiles with register caps
-// for 4 or 3 CTAs per SM and up-to-256-thread tiles without cap, over x-range
+// for 4 or 3 CTAs per SM, 224-thread tiles for 2 (the double-float sweep's
+// converter warp makes them 256) and up-to-256-thread tiles without cap, over x-range
 // lengths and ring depths that fit the shared memory of those CTAs.
 std::vector<SweepCfg> candidates(int nz, int elem, int vec, int nf) {
   std::vector<SweepCfg> out;
   if (nz % vec || (nz * elem) % 16) return out;
   const int kb = nz / vec;
-  for (int occ : {4, 3, 1}) {
-    const int threads = occ == 1 ? 256 : 128;
+  for (int occ : {4, 3, 2, 1}) {
+    const int threads = occ == 1 ? 256 : occ == 2 ? 224 : 128;
     if (kb > threads) continue;
     int ty = threads / kb;
     while (ty > 1 && (ty * kb) % 32) --ty;
@@ -243,7 +247,14 @@ cudaError_t tune_single(advect_ctx& ctx, int adj, const FwdArgs* fa, const AdjAr
 SweepCfg default_fwd_sweep(int nz, int dtype) {
   const int elem = elem_of(dtype);
   SweepCfg c = default_sweep(nz, elem);
-  if (dtype == kF64FF && c.ty > 0 && c.ty * (nz / sweep_vec(elem)) <= 128) {
+  if (dtype == kF64FF && c.ty > 0 && ff_sweep_fits(nz)) {
+    // converter-warp sweep: seven compute warps and the converter warp, two
+    // CTAs per SM (128 registers a thread), a ring of up to 8 slots
+    c.ty = 224 / (nz / sweep_vec(elem));
+    c.occ = 2;
+    c.nb = 8;
+    while (c.nb > 4 && sweep_smem_bytes(nz, elem, c) + sweep::ff_extra_bytes(c.nb, nz) > 110 * 1024) --c.nb;
+  } else if (dtype == kF64FF && c.ty > 0 && c.ty * (nz / sweep_vec(elem)) <= 128) {
     // double-float arithmetic is bound by the binary32 issue rate: four CTAs
     // per SM with the code compiled for <= 128 registers (a few spilled
     // values) and a ring that lets four fit (measured at 2048 x 2048 x 64:

@@ -13,6 +13,7 @@
 #include <type_traits>
 
 #include "sweep_core.cuh"
+#include "sweep_ff.cuh"
 #include "sweep_h16.cuh"
 
 namespace advect {
@@ -110,6 +111,51 @@ cudaError_t launch_h16_occ(const SweepParams& p, dim3 grid, int threads, size_t 
   return launch_h16_v<OCC, false>(p, grid, threads, smem, st);
 }
 
+// Double-float source terms where a column's k-blocks divide a warp: the
+// converter-warp sweep of sweep_ff.cuh (p.kb = nz / 2; kConverters more
+// warps than the tile's compute threads; ff_max_threads(OCC) threads at most).
+template <int OCC>
+__global__ void __launch_bounds__(sweep::ff_max_threads(OCC), OCC) fwd_ff_kernel(SweepParams p) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const sweep::Ring R = sweep::make_ring(smem_raw, p.nb, p.slot_cap);
+  sweep::Tile<f64ff> t;
+  t.f[0] = (const f64ff*)p.a.u;
+  t.f[1] = (const f64ff*)p.a.v;
+  t.f[2] = (const f64ff*)p.a.w;
+  t.nf = 3;
+  t.o[0] = (f64ff*)p.a.su;
+  t.o[1] = (f64ff*)p.a.sv;
+  t.o[2] = (f64ff*)p.a.sw;
+  t.nx = p.a.s.nx;
+  t.ny = p.a.s.ny;
+  t.nz = p.a.s.nz;
+  t.j0 = blockIdx.x * p.ty;
+  t.ty = p.ty;
+  t.kb = p.kb;
+  t.i_lo = p.a.i0 + blockIdx.y * p.lx;
+  t.i_hi = min(t.i_lo + p.lx, p.a.i1);
+  t.c = p.a.c;
+  t.sc = p.a.sc;
+  t.f64_levels = 0;
+  t.wait_budget = p.a.wait_budget;
+  t.skip_plane = p.a.skip_plane;
+  sweep::forward_tile_ff(t, R, p.flag);
+}
+
+template <int OCC>
+cudaError_t launch_ff_v(const SweepParams& p, dim3 grid, int threads, size_t smem, cudaStream_t st) {
+  if (threads > sweep::ff_max_threads(OCC)) return cudaErrorInvalidConfiguration;
+  static int attr_bytes = -1;
+  if ((int)smem > attr_bytes) {
+    cudaError_t e =
+        cudaFuncSetAttribute(fwd_ff_kernel<OCC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_bytes = (int)smem;
+  }
+  fwd_ff_kernel<OCC><<<grid, threads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
 template <typename T, int OCC, bool F64Z, bool SPLIT, bool INTEG>
 cudaError_t launch_v(const SweepParams& p, dim3 grid, int threads, size_t smem, cudaStream_t st) {
   if (threads > (OCC == 1 ? 256 : 128)) return cudaErrorInvalidConfiguration;
@@ -165,6 +211,27 @@ cudaError_t launch_t(const FwdArgs& a, const SweepCfg& cfg_in, int* flag, cudaSt
     // generic sweep with 4-level binary16 vectors: its own default tile
     cfg = fit_planes(default_sweep_vec(a.s.nz, (int)sizeof(__half), P), a.i1 - a.i0);
     if (cfg.ty == 0) return launch_fwd_point(kF16S, a, st);
+  }
+  if constexpr (std::is_same<T, f64ff>::value && !INTEG) {
+    if (ff_sweep_fits(a.s.nz) && cfg.ty * (a.s.nz / P) + 32 * sweep::kConverters <= sweep::ff_max_threads(cfg.occ)) {
+      SweepParams p;
+      p.a = a;
+      p.ty = cfg.ty;
+      p.kb = a.s.nz / P;
+      p.lx = cfg.lx;
+      p.nb = cfg.nb;
+      p.slot_cap = (size_t)3 * (cfg.ty + 2) * a.s.nz * sizeof(f64ff);
+      p.flag = flag;
+      const size_t smem = sweep_smem_bytes(a.s.nz, (int)sizeof(f64ff), cfg) + sweep::ff_extra_bytes(cfg.nb, a.s.nz);
+      const dim3 grid((a.s.ny + cfg.ty - 1) / cfg.ty, (a.i1 - a.i0 + cfg.lx - 1) / cfg.lx);
+      const int threads = cfg.ty * p.kb + 32 * sweep::kConverters;
+      switch (cfg.occ) {
+        case 4: return launch_ff_v<4>(p, grid, threads, smem, st);
+        case 3: return launch_ff_v<3>(p, grid, threads, smem, st);
+        case 2: return launch_ff_v<2>(p, grid, threads, smem, st);
+        default: return launch_ff_v<1>(p, grid, threads, smem, st);
+      }
+    }
   }
   SweepParams p;
   p.a = a;

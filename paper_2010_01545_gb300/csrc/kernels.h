@@ -54,6 +54,9 @@ cudaError_t launch_adj_point(int dtype, const AdjArgs& a, cudaStream_t st);
 // aligned fields, ty * nz / sweep_vec(elem) a multiple of 32 and <= 256.
 int sweep_vec(int elem);
 size_t sweep_smem_bytes(int nz, int elem, const SweepCfg& cfg);
+// The double-float forward uses its converter-warp sweep (sweep_ff.cuh) when
+// a column's 2-level k-blocks divide a warp (nz = 2, 4, ..., 64).
+inline bool ff_sweep_fits(int nz) { return nz % 2 == 0 && nz / 2 <= 32 && 32 % (nz / 2) == 0; }
 // Default tile for vectors of vec levels per thread (ty == 0: not sweepable).
 SweepCfg default_sweep_vec(int nz, int elem, int vec);
 // A sweep launch is (ceil(ny / ty), ceil(planes / lx)) CTAs and gridDim.y is

@@ -1,0 +1,369 @@
+// sweep_ff.cuh -- plane-sweep tile of the forward for binary64 storage with
+// double-float arithmetic (ADVECT_F64_FF), columns whose rows fit in a warp.
+//
+// Same ring of bulk-copied slabs and bounded waits as the generic sweep
+// (sweep_core.cuh).  What differs:
+//
+//  * A converter warp (the CTA's last) splits every landed slab once, in
+//    place: each pair of binary64 values (levels k, k+1, k even) becomes the
+//    16 bytes (hi_k, hi_k+1, lo_k, lo_k+1) of binary32 numbers (ff.cuh's
+//    split), and the warp then arrives on the slot's conversion mbarrier.
+//    The compute warps wait on that barrier instead of the copy's, so a
+//    binary64 value is split once per CTA rather than by each of the (up to
+//    three) threads that read it, and the compute warps keep drifting within
+//    the ring independently of each other (the converter runs ahead).
+//  * A compute thread owns the levels (k0, k0+1) of one column, and the
+//    double-float arithmetic of both levels runs in two-wide binary32
+//    instructions (__fadd2_rn, __fmul2_rn, __ffma2_rn: one instruction for
+//    both levels), on register pairs laid out as the converted slab is.
+//  * Registers, not shared-memory bandwidth, limit the sweep: nothing is
+//    carried across planes (plane i-1's slot stays resident until plane i is
+//    done), every vector is re-read from shared memory by the source term
+//    that uses it (volatile loads, which the compiler cannot merge), and the
+//    split constants (vertical coefficients, tcx, tcy) sit in a shared table.
+//    That fits the code in 128 registers without spills, so two CTAs of
+//    seven compute warps and the converter run per SM.
+//
+// Double-float sums are TwoSum of the high parts with the low parts added,
+// products the exact product of the high parts (FMA) plus the two cross
+// terms, as in ff.cuh (no renormalisation until the result is assembled into
+// a binary64 value).  Levels below and above the column: the halo below is
+// read only by level 0, whose three outputs are written as zero, and the
+// halo above only by level nz-1, where sw is written as zero and su, sv
+// multiply it by tzc2(nz-1) = 0, so only the u and v halos above are zeroed.
+#pragma once
+
+#include "sweep_core.cuh"
+
+namespace advect {
+namespace sweep {
+namespace ffx {
+
+constexpr int P = 2;
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b, rounded once
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+// Two levels of double-float values: level k in (hi.x, lo.x), k+1 in (hi.y, lo.y).
+struct FF2 {
+  float2 hi, lo;
+};
+
+// one level: hi + lo
+struct F1 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF2 add(const FF2& a, const FF2& b) {
+  const float2 s = add2(a.hi, b.hi);
+  const float2 bb = sub2(s, a.hi);
+  const float2 e = add2(sub2(a.hi, sub2(s, bb)), sub2(b.hi, bb));
+  return FF2{s, add2(e, add2(a.lo, b.lo))};
+}
+
+// a - b: TwoSum of a.hi and -b.hi (b.hi + bb is exactly -(-b.hi - bb))
+__device__ __forceinline__ FF2 sub(const FF2& a, const FF2& b) {
+  const float2 s = sub2(a.hi, b.hi);
+  const float2 bb = sub2(s, a.hi);
+  const float2 e = sub2(sub2(a.hi, sub2(s, bb)), add2(b.hi, bb));
+  return FF2{s, add2(e, sub2(a.lo, b.lo))};
+}
+
+__device__ __forceinline__ FF2 mul(const FF2& a, const FF2& b) {
+  const float2 p = mul2(a.hi, b.hi);
+  float2 e = fma2(a.hi, b.hi, make_float2(-p.x, -p.y));  // exact error of p (negation folded into the FMA)
+  e = fma2(a.hi, b.lo, e);
+  e = fma2(a.lo, b.hi, e);
+  return FF2{p, e};
+}
+
+// The pair shifted down one level: (level k0-1 from below, level k0).
+__device__ __forceinline__ FF2 zm(const FF2& v, const F1& below) {
+  return FF2{make_float2(below.hi, v.hi.x), make_float2(below.lo, v.lo.x)};
+}
+// The pair shifted up one level: (level k0+1, level k0+2 from above).
+__device__ __forceinline__ FF2 zp(const FF2& v, const F1& above) {
+  return FF2{make_float2(v.hi.y, above.hi), make_float2(v.lo.y, above.lo)};
+}
+
+
+// Vertical halos from the neighbouring lanes (rows do not straddle warps).
+__device__ __forceinline__ F1 below(const FF2& v) {
+  return F1{__shfl_up_sync(0xffffffffu, v.hi.y, 1), __shfl_up_sync(0xffffffffu, v.lo.y, 1)};
+}
+template <bool ZERO>
+__device__ __forceinline__ F1 above(const FF2& v, bool top) {
+  F1 r{__shfl_down_sync(0xffffffffu, v.hi.x, 1), __shfl_down_sync(0xffffffffu, v.lo.x, 1)};
+  if (ZERO && top) r = F1{0.f, 0.f};
+  return r;
+}
+
+__device__ __forceinline__ float4 lds128(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
+}
+// A raw slab pair of binary64 values and a converted 16-byte vector, by
+// shared address (the converter warps' in-place split).
+__device__ __forceinline__ double2 lds_f64x2(uint32_t a) {
+  double2 v;
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts128(uint32_t a, float4 v) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+               : "memory");
+}
+
+// A converted slab vector or table entry (16 bytes: hi_k, hi_k+1, lo_k,
+// lo_k+1) at shared address a.  The load is volatile: the compiler re-reads
+// a vector where it is used instead of holding it across the three source
+// terms (registers, not shared-memory bandwidth, limit the sweep).
+__device__ __forceinline__ FF2 ldc(uint32_t a) {
+  const float4 v = lds128(a);
+  return FF2{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+
+// A level pair of a per-level binary64 table, split.
+__device__ __forceinline__ FF2 coef2(const double* tab, int k) {
+  const ff a(__ldg(tab + k)), b(__ldg(tab + k + 1));
+  return FF2{make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)};
+}
+
+__device__ __forceinline__ FF2 bcast(const ff& x) { return FF2{make_float2(x.hi, x.hi), make_float2(x.lo, x.lo)}; }
+
+// (hi, lo) of one level -> binary64, rounded once: the high part converted
+// on the binary64 pipe, the low part by integer bit operations (a normal
+// binary32 value rebiased into binary64; zero and binary32 subnormals, below
+// 2^-126, as zero), then one binary64 add.
+__device__ __forceinline__ double assemble(float hi, float lo) {
+  const uint32_t b = __float_as_uint(lo);
+  const uint32_t mag = b & 0x7fffffffu;
+  const uint32_t top = ((mag >> 3) + 0x38000000u) | (b & 0x80000000u);
+  const uint32_t bot = b << 29;
+  const bool zero = mag < 0x00800000u;
+  const double l = __hiloint2double((int)(zero ? (b & 0x80000000u) : top), (int)(zero ? 0u : bot));
+  return (double)hi + l;
+}
+
+}  // namespace ffx
+
+// Converter warps per CTA (after the compute warps).
+constexpr int kConverters = 1;
+
+// Threads a CTA of the converter-warp sweep may have at a given number of
+// CTAs per SM (the register file is split between the SM's four schedulers:
+// 5 warps x 3 CTAs and 8 warps x 2 CTAs both leave 128 registers a thread).
+__host__ __device__ constexpr int ff_max_threads(int occ) { return occ >= 3 ? 160 : 256; }
+
+// Shared-memory bytes after the ring: the split constants (the four vertical
+// coefficient tables as level pairs, rows [c1 | c2 | d1 | d2] of nz / 2
+// entries, then tcx and tcy broadcast to both levels; 16 bytes an entry) and
+// the conversion mbarriers.
+__host__ __device__ inline size_t ff_const_bytes(int nz) { return (size_t)(2 * nz + 2) * 16; }
+__host__ __device__ inline size_t ff_extra_bytes(int nb, int nz) {
+  return ff_const_bytes(nz) + (size_t)nb * sizeof(uint64_t);
+}
+
+// Sweep one double-float tile with blockDim.x = t.ty * t.kb + 32 kConverters
+// threads: the compute warps first, the converter warps last.  t.kb = nz / 2
+// divides 32.
+__device__ inline bool forward_tile_ff(const Tile<f64ff>& t, const Ring& R, int* flag) {
+  using namespace ffx;
+  const int NB = R.nb;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int nz = t.nz, ty = t.ty, ny = t.ny;
+  const int KB = nz / P;
+  const int compute_threads = ty * KB;  // a multiple of 32
+  const int nwarps = compute_threads >> 5;
+  const int nplanes = t.i_hi - t.i_lo + 2;
+  const int rows = ty + 2;
+  const uint32_t cap = (uint32_t)R.slot_cap;  // slot stride
+  const uint32_t ring = (uint32_t)__cvta_generic_to_shared(R.slots);
+  float4* ctab = reinterpret_cast<float4*>(R.slots + ring_bytes(R.nb, R.slot_cap));
+  uint64_t* conv = reinterpret_cast<uint64_t*>(ctab + 2 * nz + 2);
+  if (tid == 0)  // made visible by start_tile's fence and barrier
+    for (int s = 0; s < NB; ++s) mbar_init(&conv[s], kConverters);
+  // the split constants (visible after start_tile's barrier)
+  for (int e = tid; e < 2 * nz + 2; e += blockDim.x) {
+    FF2 c;
+    if (e < 4 * KB) {
+      const int m = e / KB, kp = e - m * KB;
+      const int tab = m == 0 ? TZC1 : m == 1 ? TZC2 : m == 2 ? TZD1 : TZD2;
+      c = coef2(t.c.d + tab * nz, 2 * kp);
+    } else {
+      c = bcast(ff(e == 4 * KB ? t.c.tcx : t.c.tcy));
+    }
+    ctab[e] = make_float4(c.hi.x, c.hi.y, c.lo.x, c.lo.y);
+  }
+  start_tile<3>(t, R, nplanes);
+  int timed_out = 0;
+  if (tid >= compute_threads) {
+    // converter warps: split each slab in place, in plane order; each of the
+    // kConverters warps takes every kConverters-th pair and arrives on the
+    // slot's conversion barrier (expected arrivals: kConverters)
+    const int pairs = 3 * rows * nz / 2;
+    const int cw = (tid - compute_threads) >> 5;  // converter warp index
+    const int stride = 32 * kConverters;
+    SlotPos q{0, 0};
+    for (int ql = 0; ql < nplanes; ++ql) {
+      if (!mbar_wait_bounded(&R.full[q.slot], (uint32_t)(q.use & 1), t.wait_budget)) {
+        atomicExch(flag, 1);
+        timed_out = 1;
+      }
+      if (__any_sync(0xffffffffu, timed_out)) break;
+      const uint32_t sb = ring + (uint32_t)q.slot * cap;
+      int e = cw * 32 + lane;
+      // four pairs at a time: loads first, then the splits, then the stores
+      for (; e + 3 * stride < pairs; e += 4 * stride) {
+        double2 d[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) d[u] = lds_f64x2(sb + (uint32_t)(e + u * stride) * 16u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const ff a(d[u].x), b(d[u].y);
+          sts128(sb + (uint32_t)(e + u * stride) * 16u, make_float4(a.hi, b.hi, a.lo, b.lo));
+        }
+      }
+      for (; e < pairs; e += stride) {
+        const double2 d = lds_f64x2(sb + (uint32_t)e * 16u);
+        const ff a(d.x), b(d.y);
+        sts128(sb + (uint32_t)e * 16u, make_float4(a.hi, b.hi, a.lo, b.lo));
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&conv[q.slot]);
+      q.next(NB);
+    }
+  } else {
+    const int kb = tid % KB, rr = tid / KB;
+    const int k0 = kb * P;
+    const int j = t.j0 + rr;
+    const bool row_ok = j < ny;
+    const bool top = kb == KB - 1;
+    const bool bottom = kb == 0;
+    const int r = rr + 1;
+    // byte offsets in a slab: this thread's u vector, one row, one field
+    const uint32_t o_u0 = (uint32_t)(r * nz + k0) * 8u, o_row8 = (uint32_t)nz * 8u;
+    const uint32_t o_fld = (uint32_t)rows * o_row8;
+    auto wait = [&](SlotPos q) {
+      if (!mbar_wait_bounded(&conv[q.slot], (uint32_t)(q.use & 1), t.wait_budget)) {
+        atomicExch(flag, 1);
+        timed_out = 1;
+      }
+    };
+    auto release = [&](int ql, SlotPos q) { release_plane<3>(t, R, ql, q, nplanes, nwarps, lane); };
+    // shared addresses of this thread's constants
+    const uint32_t a_c1 = (uint32_t)__cvta_generic_to_shared(ctab + kb);
+    const uint32_t a_tc = (uint32_t)__cvta_generic_to_shared(ctab + 4 * KB);
+    const size_t plane_elems = (size_t)ny * nz;
+    const size_t o_row = (size_t)j * nz + k0;
+
+    // slots of planes i-1, i, i+1; nothing but these is carried across
+    // planes: every vector is read from shared memory where it is used
+    SlotPos pm{0, 0}, pc{0, 0}, pn{0, 0};
+    pc.next(NB);
+    pn = pc;
+    pn.next(NB);
+    wait(pm);
+    wait(pc);
+    for (int i = t.i_lo; i < t.i_hi; ++i) {
+      wait(pn);
+      if (__any_sync(0xffffffffu, timed_out)) break;
+      // this thread's u vector in the slabs of planes i-1, i, i+1
+      const uint32_t Pm = ring + (uint32_t)pm.slot * cap + o_u0;
+      const uint32_t Pc = ring + (uint32_t)pc.slot * cap + o_u0;
+      const uint32_t Pn = ring + (uint32_t)pn.slot * cap + o_u0;
+      const uint32_t o_um = 0u - o_row8, o_up = o_row8, o_v0 = o_fld, o_vm = o_fld - o_row8, o_vp = o_fld + o_row8;
+      const uint32_t o_w0 = 2u * o_fld, o_wm = 2u * o_fld - o_row8, o_wp = 2u * o_fld + o_row8;
+      const size_t o = (size_t)i * plane_elems + o_row;
+      // su (Listing 1)
+      {
+        const FF2 U0 = ldc(Pc), UXM = ldc(Pm), UXP = ldc(Pn);
+        const FF2 W0 = ldc(Pc + o_w0), WXP = ldc(Pn + o_w0);
+        const FF2 UYM = ldc(Pc + o_um), VYM = ldc(Pc + o_vm), VXPYM = ldc(Pn + o_vm);
+        const FF2 UYP = ldc(Pc + o_up), V0 = ldc(Pc + o_v0), VXP = ldc(Pn + o_v0);
+        const FF2 uzm = zm(U0, below(U0)), uzp = zp(U0, above<true>(U0, top));
+        // vertical faces: the lower face of level k is the upper face of
+        // level k-1 (the lane below holds it for the first level)
+        const FF2 wu_hi = add(W0, WXP);
+        const FF2 wu_lo = zm(wu_hi, below(wu_hi));
+        const FF2 xu = sub(mul(UXM, add(UXM, U0)), mul(UXP, add(U0, UXP)));
+        const FF2 yu = sub(mul(UYM, add(VYM, VXPYM)), mul(UYP, add(V0, VXP)));
+        FF2 hu = add(mul(ldc(a_tc), xu), mul(ldc(a_tc + 16), yu));
+        hu = add(hu, mul(mul(ldc(a_c1), uzm), wu_lo));
+        hu = sub(hu, mul(mul(ldc(a_c1 + 16 * KB), uzp), wu_hi));
+        if (row_ok) {  // su at level 0 is zero
+          const double u0 = bottom ? 0.0 : assemble(hu.hi.x, hu.lo.x), u1 = assemble(hu.hi.y, hu.lo.y);
+          __stcs(reinterpret_cast<double2*>(t.o[0]) + o / 2, make_double2(u0, u1));
+        }
+      }
+      // sv
+      {
+        const FF2 V0 = ldc(Pc + o_v0), VXM = ldc(Pm + o_v0), VXP = ldc(Pn + o_v0);
+        const FF2 UXM = ldc(Pm), UXMYP = ldc(Pm + o_up), U0 = ldc(Pc), UYP = ldc(Pc + o_up);
+        const FF2 VYM = ldc(Pc + o_vm), VYP = ldc(Pc + o_vp);
+        const FF2 W0 = ldc(Pc + o_w0), WYP = ldc(Pc + o_wp);
+        const FF2 vzm = zm(V0, below(V0)), vzp = zp(V0, above<true>(V0, top));
+        const FF2 wv_hi = add(W0, WYP);
+        const FF2 wv_lo = zm(wv_hi, below(wv_hi));
+        const FF2 xv = sub(mul(VXM, add(UXM, UXMYP)), mul(VXP, add(U0, UYP)));
+        const FF2 yv = sub(mul(VYM, add(V0, VYM)), mul(VYP, add(V0, VYP)));
+        FF2 hv = add(mul(ldc(a_tc), xv), mul(ldc(a_tc + 16), yv));
+        hv = add(hv, mul(mul(ldc(a_c1), vzm), wv_lo));
+        hv = sub(hv, mul(mul(ldc(a_c1 + 16 * KB), vzp), wv_hi));
+        if (row_ok) {  // sv at level 0 is zero
+          const double v0 = bottom ? 0.0 : assemble(hv.hi.x, hv.lo.x), v1 = assemble(hv.hi.y, hv.lo.y);
+          __stcs(reinterpret_cast<double2*>(t.o[1]) + o / 2, make_double2(v0, v1));
+        }
+      }
+      // sw
+      {
+        const FF2 W0 = ldc(Pc + o_w0), WXM = ldc(Pm + o_w0), WXP = ldc(Pn + o_w0);
+        const FF2 UXM = ldc(Pm), U0 = ldc(Pc);
+        const FF2 WYM = ldc(Pc + o_wm), VYM = ldc(Pc + o_vm), WYP = ldc(Pc + o_wp), V0 = ldc(Pc + o_v0);
+        const FF2 wzm = zm(W0, below(W0)), wzp = zp(W0, above<false>(W0, top));
+        const FF2 ww_hi = add(W0, wzp);
+        const FF2 ww_lo = zm(ww_hi, below(ww_hi));
+        const FF2 uzp = zp(U0, above<true>(U0, top)), vzp = zp(V0, above<true>(V0, top));
+        const FF2 xw = sub(mul(WXM, add(UXM, zp(UXM, above<false>(UXM, top)))), mul(WXP, add(U0, uzp)));
+        const FF2 yw = sub(mul(WYM, add(VYM, zp(VYM, above<false>(VYM, top)))), mul(WYP, add(V0, vzp)));
+        FF2 hw = add(mul(ldc(a_tc), xw), mul(ldc(a_tc + 16), yw));
+        hw = add(hw, mul(mul(ldc(a_c1 + 32 * KB), wzm), ww_lo));
+        hw = sub(hw, mul(mul(ldc(a_c1 + 48 * KB), wzp), ww_hi));
+        if (row_ok) {  // sw at levels 0 and nz-1 is zero
+          const double w0 = bottom ? 0.0 : assemble(hw.hi.x, hw.lo.x);
+          const double w1 = top ? 0.0 : assemble(hw.hi.y, hw.lo.y);
+          __stcs(reinterpret_cast<double2*>(t.o[2]) + o / 2, make_double2(w0, w1));
+        }
+      }
+      // plane i-1 is no longer read by this warp
+      release(i - t.i_lo, pm);
+      pm = pc;
+      pc = pn;
+      pn.next(NB);
+    }
+  }
+  // end of the tile (all threads): on a timeout wait (bounded) for the last
+  // copy issued into each slot; otherwise invalidate the slots' barriers so
+  // that the ring can be re-initialised
+  const int any_fail = __syncthreads_or(timed_out);
+  if (tid == 0) {
+    for (int s = 0; s < NB; ++s) {
+      const int n = R.issued[s];
+      if (any_fail) {
+        if (n > 0) mbar_wait_bounded(&R.full[s], (uint32_t)((n - 1) & 1), 1 << 20);
+      } else {
+        mbar_inval(&R.full[s]);
+        mbar_inval(&conv[s]);
+      }
+    }
+  }
+  __syncthreads();
+  return !any_fail;
+}
+
+}  // namespace sweep
+}  // namespace advect

@@ -10,7 +10,7 @@ from gpu_util import dev, host, make_op, normwise, oracle_adjoint, oracle_forwar
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(64, 64, 64), (33, 17, 65), (130, 66, 20), (5, 7, 3), (1, 1, 4), (16, 32, 128)]
+SHAPES = [(64, 64, 64), (33, 17, 65), (130, 66, 20), (5, 7, 3), (1, 1, 4), (16, 32, 128), (23, 19, 32), (9, 40, 16)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
