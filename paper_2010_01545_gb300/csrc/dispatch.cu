@@ -84,6 +84,19 @@ static void sweep_override(const char* var, SweepCfg& c, int nz, int elem, int v
   c = o;
 }
 
+// ADVECT_ADJ_SWEEP "ty,lx,nb[,occ]" for the double-float adjoint's own sweep
+// (two levels per thread); false (nothing changed) unless set and valid there.
+static bool adj_ff_override(SweepCfg& c, int nz) {
+  const char* s = getenv("ADVECT_ADJ_SWEEP");
+  if (!s) return false;
+  SweepCfg o{0, 0, 0, 1};
+  const int n = sscanf(s, "%d,%d,%d,%d", &o.ty, &o.lx, &o.nb, &o.occ);
+  if (n < 3 || !adj_ff_fits(nz, o)) return false;
+  o.occ = 1;
+  c = o;
+  return true;
+}
+
 // Default adjoint tile (six streamed fields): 128 threads with registers
 // capped for four CTAs per SM (binary32) or three (8-byte types: binary64
 // and double-float; measured at 1024 x 1024 x 128 against one uncapped
@@ -223,7 +236,11 @@ cudaError_t tune_single(advect_ctx& ctx, int adj, const FwdArgs* fa, const AdjAr
   }, e);
   if (e != cudaSuccess) return e;
   if (!(adj && ctx.dtype == ADVECT_F16S)) {
-    for (const SweepCfg& c : candidates(m.nz, elem, vec, nf)) {
+    // the context's current tile competes too (the double-float adjoint's
+    // default is not among the generic candidates)
+    std::vector<SweepCfg> cands = candidates(m.nz, elem, vec, nf);
+    if (kind == 1) cands.insert(cands.begin(), cfg);
+    for (const SweepCfg& c : cands) {
       const float ms = time_ms(st, [&]() {
         return adj ? launch_adj_sweep((int)ctx.dtype, *aa, fit_planes(c, aa->s.nx), ctx.d_flag, st)
                    : launch_fwd_sweep((int)ctx.dtype, *fa, fit_planes(c, fa->i1 - fa->i0), ctx.d_flag, st);
@@ -278,7 +295,11 @@ void select_kernels(advect_ctx& ctx) {
   ctx.fwd_kind = ctx.sweep.ty > 0 ? 1 : 0;
   ctx.fwd_name = ctx.fwd_kind ? "fwd_sweep" : "fwd_point";
   ctx.adj_sweep = default_adj_sweep(m.nz, elem);
-  if (ctx.dtype == ADVECT_F64_FF && ctx.adj_sweep.ty > 0) {
+  const SweepCfg aff = ctx.dtype == ADVECT_F64_FF ? default_adj_ff(m.nz) : SweepCfg{0, 0, 0, 1};
+  if (aff.ty > 0) {
+    // double-float adjoint with its own sweep (adj_ff.cuh)
+    ctx.adj_sweep = aff;
+  } else if (ctx.dtype == ADVECT_F64_FF && ctx.adj_sweep.ty > 0) {
     // double-float adjoint: 128-plane tiles where the grid still gives at
     // least eight CTAs per resident slot on the device's SMs (measured on
     // 152 SMs: 16.2 against 15.8 Gpts/s at 1024 x 1024 x 128; at 512 x 512 x
@@ -287,7 +308,8 @@ void select_kernels(advect_ctx& ctx) {
     const long long ctas = (long long)((m.nx + 127) / 128) * ((m.ny + ctx.adj_sweep.ty - 1) / ctx.adj_sweep.ty);
     if (ctas >= 8LL * ctx.sms * ctx.adj_sweep.occ) ctx.adj_sweep.lx = 128;
   }
-  sweep_override("ADVECT_ADJ_SWEEP", ctx.adj_sweep, m.nz, elem, adj_sweep_vec(elem), 6);
+  if (!(aff.ty > 0 && adj_ff_override(ctx.adj_sweep, m.nz)))
+    sweep_override("ADVECT_ADJ_SWEEP", ctx.adj_sweep, m.nz, elem, adj_sweep_vec(elem), 6);
   ctx.adj_kind = ctx.adj_sweep.ty > 0 ? 1 : 0;
   // a tuned choice from the cache wins over the defaults; an environment
   // override wins over both

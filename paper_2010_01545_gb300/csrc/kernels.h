@@ -74,6 +74,10 @@ cudaError_t launch_fwd_sweep_integ(int dtype, const FwdArgs& a, const SweepCfg& 
 // Adjoint plane sweep (F64, F32): nz % adj_sweep_vec(elem) == 0, nz * elem % 16
 // == 0, 16-byte aligned fields, ty * nz / adj_sweep_vec(elem) a multiple of 32.
 int adj_sweep_vec(int elem);
+// The double-float adjoint's own sweep (adj_ff.cuh, two levels per thread):
+// whether a tile fits it, and its default tile (ty = 0: the shape does not).
+bool adj_ff_fits(int nz, const SweepCfg& c);
+SweepCfg default_adj_ff(int nz);
 size_t adj_sweep_smem_bytes(int nz, int elem, const SweepCfg& cfg);
 cudaError_t launch_adj_sweep(int dtype, const AdjArgs& a, const SweepCfg& cfg, int* flag, cudaStream_t st);
 
