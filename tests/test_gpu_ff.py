@@ -63,3 +63,25 @@ def test_ff_sweep_configs(monkeypatch):
         out = op.forward(*(dev(a) for a in x))
         for g, r in zip(out, oracle_forward(*x, grid)):
             assert normwise(host(g), r) <= 1e-12, cfg
+
+
+@pytest.mark.parametrize("shape,cfgs", [
+    # 128 levels: a row's level pairs span two warps
+    ((37, 45, 128), [(6, 64, 4), (2, 5, 4), (3, 300, 5), (1, 7, 4)]),
+    # 64 and 16 levels: rows within a warp (one, and four rows per warp)
+    ((21, 30, 64), [(12, 64, 5), (1, 3, 4), (5, 8, 6)]),
+    ((19, 50, 16), [(48, 64, 4), (4, 2, 4)]),
+])
+def test_ff_adjoint_sweep_configs(monkeypatch, shape, cfgs):
+    """The double-float adjoint's own sweep over tile shapes: ragged rows
+    (ny not a multiple of ty), tiles of a few planes, shallow and deep rings."""
+    x = workload.winds(*shape, seed=46)
+    lam = workload.cotangents(*shape, seed=47)
+    for cfg in cfgs:
+        monkeypatch.setenv("ADVECT_ADJ_SWEEP", ",".join(map(str, cfg)))
+        op, grid = make_op(shape, "f64ff")
+        assert op.kernel_name(True) == "adj_sweep"
+        assert op.tuned_config(True).startswith("ty=%d,lx=%d,nb=%d," % cfg), (cfg, op.tuned_config(True))
+        out = op.adjoint(*(dev(a) for a in x), *(dev(a) for a in lam))
+        for g, r in zip(out, oracle_adjoint(*x, *lam, grid)):
+            assert normwise(host(g), r) <= 1e-12, cfg
