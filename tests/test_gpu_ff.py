@@ -56,10 +56,12 @@ def test_ff_wide_dynamic_range():
 def test_ff_sweep_configs(monkeypatch):
     shape = (37, 45, 64)
     x = workload.winds(*shape, seed=45)
-    for cfg in [(4, 64, 7, 3), (2, 5, 4, 1), (4, 300, 6, 1)]:
+    # the converter-warp sweep at 1, 2 (default, 7 rows), 3 and 4 CTAs per SM
+    for cfg in [(4, 64, 7, 3), (2, 5, 4, 1), (4, 300, 6, 1), (4, 64, 5, 4), (7, 9, 4, 2), (3, 64, 8, 2)]:
         monkeypatch.setenv("ADVECT_SWEEP", ",".join(map(str, cfg)))
         op, grid = make_op(shape, "f64ff")
         assert op.kernel_name() == "fwd_sweep"
+        assert op.tuned_config() == "ty=%d,lx=%d,nb=%d,occ=%d" % cfg, (cfg, op.tuned_config())
         out = op.forward(*(dev(a) for a in x))
         for g, r in zip(out, oracle_forward(*x, grid)):
             assert normwise(host(g), r) <= 1e-12, cfg
