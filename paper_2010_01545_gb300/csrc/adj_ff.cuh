@@ -16,9 +16,13 @@
 //    ql, ql+1 read, ql+2 being split, so four slots at least.
 //  * A thread owns the levels (k0, k0+1) of one column; both levels run in
 //    the two-wide binary32 instructions.
-//  * Nothing is carried across planes: every vector is read from shared
+//  * No vector is carried across planes: every vector is read from shared
 //    memory by the term that uses it (volatile loads), and the seven
 //    shifted vertical coefficient tables, tcx and tcy sit in a shared table.
+//    Only five terms a plane shares with the next are carried: a sum or
+//    product of plane i's values that reappears at plane i+1 as its x-1
+//    counterpart (lu(y+)u - lu u(y+) in dv; u + u(y+) in dv; u + u(z+),
+//    lu(z+)u and lu u(z+) in dw).
 //  * Face sums and products that reach level k from level k-1 are formed at
 //    the thread's own levels and shifted down one level by shuffle (the
 //    lower faces of the vertical terms; the w-cotangent brackets of du and
@@ -205,6 +209,20 @@ __device__ inline bool adjoint_tile_ff(const Tile<f64ff>& t, const Ring& R, int*
   convert(pn);
   wait_conv(pm);
   wait_conv(pc);
+  // terms that plane i shares with plane i+1, carried: as plane i+1's x-1
+  // terms they are QC = lu(y+)u - lu u(y+), FY = u + u(y+), FZ = u + u(z+),
+  // P1C = lu(z+)u, R1C = lu u(z+) (all of the x-1 column)
+  FF2 QC, FY, FZ, P1C, R1C;
+  {
+    const uint32_t Pm = ring + (uint32_t)pm.slot * cap + o_u0;
+    const FF2 UM = ldc(Pm), UMYP = ldc(Pm + R8), LM = ldc(Pm + 3 * F8), LMYP = ldc(Pm + 3 * F8 + R8);
+    const FF2 UMu = up(Pm, UM);
+    QC = sub(mul(LMYP, UM), mul(LM, UMYP));
+    FY = add(UM, UMYP);
+    FZ = add(UM, UMu);
+    P1C = mul(up(Pm + 3 * F8, LM), UM);
+    R1C = mul(LM, UMu);
+  }
   for (int i = t.i_lo; i < t.i_hi; ++i) {
     const int ql = i - t.i_lo + 1;
     wait_conv(pn);
@@ -265,13 +283,14 @@ __device__ inline bool adjoint_tile_ff(const Tile<f64ff>& t, const Ring& R, int*
     }
     // dv
     {
-      const FF2 U0 = ldc(Pc), UYP = ldc(Pc + R8), UM = ldc(Pm), UMYP = ldc(Pm + R8);
-      // su's y faces: lu(y+)u + lu(x-,y+)u(x-) - lu u(y+) - lu(x-)u(x-,y+)
+      const FF2 U0 = ldc(Pc), UYP = ldc(Pc + R8);
+      // su's y faces: lu(y+)u + lu(x-,y+)u(x-) - lu u(y+) - lu(x-)u(x-,y+) = Q + Q(x-)
       FF2 ay;
       {
-        const FF2 LYP = ldc(Pc + 3 * F8 + R8), LMYP = ldc(Pm + 3 * F8 + R8), L0 = ldc(Pc + 3 * F8),
-                  LM = ldc(Pm + 3 * F8);
-        ay = sub(add(mul(LYP, U0), mul(LMYP, UM)), add(mul(L0, UYP), mul(LM, UMYP)));
+        const FF2 LYP = ldc(Pc + 3 * F8 + R8), L0 = ldc(Pc + 3 * F8);
+        const FF2 q = sub(mul(LYP, U0), mul(L0, UYP));
+        ay = add(q, QC);
+        QC = q;
       }
       {
         // sv's y faces: lv(y+)(v(y+)+2v) + lv(v(y-)-v(y+)) - lv(y-)(v(y-)+2v)
@@ -296,7 +315,9 @@ __device__ inline bool adjoint_tile_ff(const Tile<f64ff>& t, const Ring& R, int*
       {
         // sv's x faces: lv(x+)(u+u(y+)) - lv(x-)(u(x-)+u(x-,y+))
         const FF2 MP = ldc(Pn + 4 * F8), MM = ldc(Pm + 4 * F8);
-        gv = add(gv, mul(tcx, sub(mul(MP, add(U0, UYP)), mul(MM, add(UM, UMYP)))));
+        const FF2 fy = add(U0, UYP);
+        gv = add(gv, mul(tcx, sub(mul(MP, fy), mul(MM, FY))));
+        FY = fy;
       }
       {
         // sv's z faces: tzc1(k+1) lv(z+)G - tzc2(k-1) lv(z-)G(z-), G = w + w(y+)
@@ -315,17 +336,18 @@ __device__ inline bool adjoint_tile_ff(const Tile<f64ff>& t, const Ring& R, int*
     }
     // dw
     {
-      const FF2 U0 = ldc(Pc), UM = ldc(Pm), V0 = ldc(Pc + F8), VYM = ldc(Pc + F8 - R8);
-      const FF2 U0u = up(Pc, U0), UMu = up(Pm, UM), V0u = up(Pc + F8, V0), VYMu = up(Pc + F8 - R8, VYM);
+      const FF2 U0 = ldc(Pc), V0 = ldc(Pc + F8), VYM = ldc(Pc + F8 - R8);
+      const FF2 U0u = up(Pc, U0), V0u = up(Pc + F8, V0), VYMu = up(Pc + F8 - R8, VYM);
       FF2 gw;
       {
         // su, sv z faces through w: tzc1(k+1)[lu(z+)u + lu(x-,z+)u(x-) + lv(z+)v + lv(y-,z+)v(y-)]
         //                         - tzc2(k)[lu u(z+) + lu(x-)u(x-,z+) + lv v(z+) + lv(y-)v(y-,z+)]
-        const FF2 L0 = ldc(Pc + 3 * F8), LM = ldc(Pm + 3 * F8), M0 = ldc(Pc + 4 * F8),
-                  MYM = ldc(Pc + 4 * F8 - R8);
-        const FF2 z1 = add(add(mul(up(Pc + 3 * F8, L0), U0), mul(up(Pm + 3 * F8, LM), UM)),
-                           add(mul(up(Pc + 4 * F8, M0), V0), mul(up(Pc + 4 * F8 - R8, MYM), VYM)));
-        const FF2 z2 = add(add(mul(L0, U0u), mul(LM, UMu)), add(mul(M0, V0u), mul(MYM, VYMu)));
+        const FF2 L0 = ldc(Pc + 3 * F8), M0 = ldc(Pc + 4 * F8), MYM = ldc(Pc + 4 * F8 - R8);
+        const FF2 p1 = mul(up(Pc + 3 * F8, L0), U0), r1 = mul(L0, U0u);
+        const FF2 z1 = add(add(p1, P1C), add(mul(up(Pc + 4 * F8, M0), V0), mul(up(Pc + 4 * F8 - R8, MYM), VYM)));
+        const FF2 z2 = add(add(r1, R1C), add(mul(M0, V0u), mul(MYM, VYMu)));
+        P1C = p1;
+        R1C = r1;
         gw = sub(mul(coef(C1U), z1), mul(coef(C20), z2));
       }
       {
@@ -333,7 +355,9 @@ __device__ inline bool adjoint_tile_ff(const Tile<f64ff>& t, const Ring& R, int*
         //                   + tcy[lw(y+)(v+v(z+)) - lw(y-)(v(y-)+v(y-,z+))]
         const FF2 NP = ldc(Pn + 5 * F8), NM = ldc(Pm + 5 * F8), NYP = ldc(Pc + 5 * F8 + R8),
                   NYM = ldc(Pc + 5 * F8 - R8);
-        const FF2 zx = sub(mul(NP, add(U0, U0u)), mul(NM, add(UM, UMu)));
+        const FF2 fz = add(U0, U0u);
+        const FF2 zx = sub(mul(NP, fz), mul(NM, FZ));
+        FZ = fz;
         const FF2 zy = sub(mul(NYP, add(V0, V0u)), mul(NYM, add(VYM, VYMu)));
         gw = add(gw, add(mul(tcx, zx), mul(tcy, zy)));
       }

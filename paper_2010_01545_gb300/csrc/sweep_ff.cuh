@@ -16,11 +16,13 @@
 //    double-float arithmetic of both levels runs in two-wide binary32
 //    instructions (__fadd2_rn, __fmul2_rn, __ffma2_rn: one instruction for
 //    both levels), on register pairs laid out as the converted slab is.
-//  * Registers, not shared-memory bandwidth, limit the sweep: nothing is
+//  * Registers, not shared-memory bandwidth, limit the sweep: no vector is
 //    carried across planes (plane i-1's slot stays resident until plane i is
 //    done), every vector is re-read from shared memory by the source term
 //    that uses it (volatile loads, which the compiler cannot merge), and the
 //    split constants (vertical coefficients, tcx, tcy) sit in a shared table.
+//    Only the three x-face sums a plane shares with the next (u(i) + u(i+1),
+//    u + u(y+1), u + u(z+1) of plane i are plane i+1's x-1 faces) are carried.
 //    That fits the code in 128 registers without spills, so two CTAs of
 //    seven compute warps and the converter run per SM.
 //
@@ -264,14 +266,25 @@ __device__ inline bool forward_tile_ff(const Tile<f64ff>& t, const Ring& R, int*
     const size_t plane_elems = (size_t)ny * nz;
     const size_t o_row = (size_t)j * nz + k0;
 
-    // slots of planes i-1, i, i+1; nothing but these is carried across
-    // planes: every vector is read from shared memory where it is used
+    // slots of planes i-1, i, i+1; every vector is read from shared memory
+    // where it is used
     SlotPos pm{0, 0}, pc{0, 0}, pn{0, 0};
     pc.next(NB);
     pn = pc;
     pn.next(NB);
     wait(pm);
     wait(pc);
+    // x faces of plane i-1 (i - 1/2), carried from the previous plane:
+    // u(i-1) + u(i), u(i-1) + u(i-1, y+1), u(i-1) + u(i-1, z+1)
+    FF2 FU, FV, FW;
+    {
+      const uint32_t Pm = ring + (uint32_t)pm.slot * cap + o_u0;
+      const uint32_t Pc = ring + (uint32_t)pc.slot * cap + o_u0;
+      const FF2 UM = ldc(Pm);
+      FU = add(UM, ldc(Pc));
+      FV = add(UM, ldc(Pm + o_row8));
+      FW = add(UM, zp(UM, above<true>(UM, top)));
+    }
     for (int i = t.i_lo; i < t.i_hi; ++i) {
       wait(pn);
       if (__any_sync(0xffffffffu, timed_out)) break;
@@ -293,7 +306,9 @@ __device__ inline bool forward_tile_ff(const Tile<f64ff>& t, const Ring& R, int*
         // level k-1 (the lane below holds it for the first level)
         const FF2 wu_hi = add(W0, WXP);
         const FF2 wu_lo = zm(wu_hi, below(wu_hi));
-        const FF2 xu = sub(mul(UXM, add(UXM, U0)), mul(UXP, add(U0, UXP)));
+        const FF2 fu = add(U0, UXP);
+        const FF2 xu = sub(mul(UXM, FU), mul(UXP, fu));
+        FU = fu;
         const FF2 yu = sub(mul(UYM, add(VYM, VXPYM)), mul(UYP, add(V0, VXP)));
         FF2 hu = add(mul(ldc(a_tc), xu), mul(ldc(a_tc + 16), yu));
         hu = add(hu, mul(mul(ldc(a_c1), uzm), wu_lo));
@@ -306,13 +321,15 @@ __device__ inline bool forward_tile_ff(const Tile<f64ff>& t, const Ring& R, int*
       // sv
       {
         const FF2 V0 = ldc(Pc + o_v0), VXM = ldc(Pm + o_v0), VXP = ldc(Pn + o_v0);
-        const FF2 UXM = ldc(Pm), UXMYP = ldc(Pm + o_up), U0 = ldc(Pc), UYP = ldc(Pc + o_up);
+        const FF2 U0 = ldc(Pc), UYP = ldc(Pc + o_up);
         const FF2 VYM = ldc(Pc + o_vm), VYP = ldc(Pc + o_vp);
         const FF2 W0 = ldc(Pc + o_w0), WYP = ldc(Pc + o_wp);
         const FF2 vzm = zm(V0, below(V0)), vzp = zp(V0, above<true>(V0, top));
         const FF2 wv_hi = add(W0, WYP);
         const FF2 wv_lo = zm(wv_hi, below(wv_hi));
-        const FF2 xv = sub(mul(VXM, add(UXM, UXMYP)), mul(VXP, add(U0, UYP)));
+        const FF2 fv = add(U0, UYP);
+        const FF2 xv = sub(mul(VXM, FV), mul(VXP, fv));
+        FV = fv;
         const FF2 yv = sub(mul(VYM, add(V0, VYM)), mul(VYP, add(V0, VYP)));
         FF2 hv = add(mul(ldc(a_tc), xv), mul(ldc(a_tc + 16), yv));
         hv = add(hv, mul(mul(ldc(a_c1), vzm), wv_lo));
@@ -325,13 +342,15 @@ __device__ inline bool forward_tile_ff(const Tile<f64ff>& t, const Ring& R, int*
       // sw
       {
         const FF2 W0 = ldc(Pc + o_w0), WXM = ldc(Pm + o_w0), WXP = ldc(Pn + o_w0);
-        const FF2 UXM = ldc(Pm), U0 = ldc(Pc);
+        const FF2 U0 = ldc(Pc);
         const FF2 WYM = ldc(Pc + o_wm), VYM = ldc(Pc + o_vm), WYP = ldc(Pc + o_wp), V0 = ldc(Pc + o_v0);
         const FF2 wzm = zm(W0, below(W0)), wzp = zp(W0, above<false>(W0, top));
         const FF2 ww_hi = add(W0, wzp);
         const FF2 ww_lo = zm(ww_hi, below(ww_hi));
         const FF2 uzp = zp(U0, above<true>(U0, top)), vzp = zp(V0, above<true>(V0, top));
-        const FF2 xw = sub(mul(WXM, add(UXM, zp(UXM, above<false>(UXM, top)))), mul(WXP, add(U0, uzp)));
+        const FF2 fw = add(U0, uzp);
+        const FF2 xw = sub(mul(WXM, FW), mul(WXP, fw));
+        FW = fw;
         const FF2 yw = sub(mul(WYM, add(VYM, zp(VYM, above<false>(VYM, top)))), mul(WYP, add(V0, vzp)));
         FF2 hw = add(mul(ldc(a_tc), xw), mul(ldc(a_tc + 16), yw));
         hw = add(hw, mul(mul(ldc(a_c1 + 32 * KB), wzm), ww_lo));
