@@ -23,6 +23,10 @@
 //    split constants (vertical coefficients, tcx, tcy) sit in a shared table.
 //    Only the three x-face sums a plane shares with the next (u(i) + u(i+1),
 //    u + u(y+1), u + u(z+1) of plane i are plane i+1's x-1 faces) are carried.
+//  * The three source terms are evaluated side by side, stage by stage (x
+//    faces of su, sv, sw, then their y faces, then the vertical faces): the
+//    double-float chains of one term depend on each other, the three terms
+//    do not, so each warp has three independent chains in flight.
 //    That fits the code in 128 registers without spills, so two CTAs of
 //    seven compute warps and the converter run per SM.
 //
@@ -295,71 +299,65 @@ __device__ inline bool forward_tile_ff(const Tile<f64ff>& t, const Ring& R, int*
       const uint32_t o_um = 0u - o_row8, o_up = o_row8, o_v0 = o_fld, o_vm = o_fld - o_row8, o_vp = o_fld + o_row8;
       const uint32_t o_w0 = 2u * o_fld, o_wm = 2u * o_fld - o_row8, o_wp = 2u * o_fld + o_row8;
       const size_t o = (size_t)i * plane_elems + o_row;
-      // su (Listing 1)
+      // su, sv, sw (Listing 1 and its v, w counterparts) stage by stage
+      FF2 hu, hv, hw;
       {
-        const FF2 U0 = ldc(Pc), UXM = ldc(Pm), UXP = ldc(Pn);
-        const FF2 W0 = ldc(Pc + o_w0), WXP = ldc(Pn + o_w0);
-        const FF2 UYM = ldc(Pc + o_um), VYM = ldc(Pc + o_vm), VXPYM = ldc(Pn + o_vm);
-        const FF2 UYP = ldc(Pc + o_up), V0 = ldc(Pc + o_v0), VXP = ldc(Pn + o_v0);
-        const FF2 uzm = zm(U0, below(U0)), uzp = zp(U0, above<true>(U0, top));
+        // x faces
+        const FF2 U0 = ldc(Pc);
+        const FF2 fu = add(U0, ldc(Pn));
+        const FF2 fv = add(U0, ldc(Pc + o_up));
+        const FF2 fw = add(U0, zp(U0, above<true>(U0, top)));
+        const FF2 xu = sub(mul(ldc(Pm), FU), mul(ldc(Pn), fu));
+        const FF2 xv = sub(mul(ldc(Pm + o_v0), FV), mul(ldc(Pn + o_v0), fv));
+        const FF2 xw = sub(mul(ldc(Pm + o_w0), FW), mul(ldc(Pn + o_w0), fw));
+        FU = fu;
+        FV = fv;
+        FW = fw;
+        const FF2 tcx = ldc(a_tc);
+        hu = mul(tcx, xu);
+        hv = mul(tcx, xv);
+        hw = mul(tcx, xw);
+      }
+      {
+        // y faces
+        const FF2 V0 = ldc(Pc + o_v0), VYM = ldc(Pc + o_vm);
+        const FF2 yu = sub(mul(ldc(Pc + o_um), add(VYM, ldc(Pn + o_vm))), mul(ldc(Pc + o_up), add(V0, ldc(Pn + o_v0))));
+        const FF2 VYP = ldc(Pc + o_vp);
+        const FF2 yv = sub(mul(VYM, add(V0, VYM)), mul(VYP, add(V0, VYP)));
+        const FF2 yw = sub(mul(ldc(Pc + o_wm), add(VYM, zp(VYM, above<false>(VYM, top)))),
+                           mul(ldc(Pc + o_wp), add(V0, zp(V0, above<true>(V0, top)))));
+        const FF2 tcy = ldc(a_tc + 16);
+        hu = add(hu, mul(tcy, yu));
+        hv = add(hv, mul(tcy, yv));
+        hw = add(hw, mul(tcy, yw));
+      }
+      {
         // vertical faces: the lower face of level k is the upper face of
         // level k-1 (the lane below holds it for the first level)
-        const FF2 wu_hi = add(W0, WXP);
-        const FF2 wu_lo = zm(wu_hi, below(wu_hi));
-        const FF2 fu = add(U0, UXP);
-        const FF2 xu = sub(mul(UXM, FU), mul(UXP, fu));
-        FU = fu;
-        const FF2 yu = sub(mul(UYM, add(VYM, VXPYM)), mul(UYP, add(V0, VXP)));
-        FF2 hu = add(mul(ldc(a_tc), xu), mul(ldc(a_tc + 16), yu));
-        hu = add(hu, mul(mul(ldc(a_c1), uzm), wu_lo));
-        hu = sub(hu, mul(mul(ldc(a_c1 + 16 * KB), uzp), wu_hi));
-        if (row_ok) {  // su at level 0 is zero
-          const double u0 = bottom ? 0.0 : assemble(hu.hi.x, hu.lo.x), u1 = assemble(hu.hi.y, hu.lo.y);
-          __stcs(reinterpret_cast<double2*>(t.o[0]) + o / 2, make_double2(u0, u1));
-        }
-      }
-      // sv
-      {
-        const FF2 V0 = ldc(Pc + o_v0), VXM = ldc(Pm + o_v0), VXP = ldc(Pn + o_v0);
-        const FF2 U0 = ldc(Pc), UYP = ldc(Pc + o_up);
-        const FF2 VYM = ldc(Pc + o_vm), VYP = ldc(Pc + o_vp);
-        const FF2 W0 = ldc(Pc + o_w0), WYP = ldc(Pc + o_wp);
-        const FF2 vzm = zm(V0, below(V0)), vzp = zp(V0, above<true>(V0, top));
-        const FF2 wv_hi = add(W0, WYP);
-        const FF2 wv_lo = zm(wv_hi, below(wv_hi));
-        const FF2 fv = add(U0, UYP);
-        const FF2 xv = sub(mul(VXM, FV), mul(VXP, fv));
-        FV = fv;
-        const FF2 yv = sub(mul(VYM, add(V0, VYM)), mul(VYP, add(V0, VYP)));
-        FF2 hv = add(mul(ldc(a_tc), xv), mul(ldc(a_tc + 16), yv));
-        hv = add(hv, mul(mul(ldc(a_c1), vzm), wv_lo));
-        hv = sub(hv, mul(mul(ldc(a_c1 + 16 * KB), vzp), wv_hi));
-        if (row_ok) {  // sv at level 0 is zero
-          const double v0 = bottom ? 0.0 : assemble(hv.hi.x, hv.lo.x), v1 = assemble(hv.hi.y, hv.lo.y);
-          __stcs(reinterpret_cast<double2*>(t.o[1]) + o / 2, make_double2(v0, v1));
-        }
-      }
-      // sw
-      {
-        const FF2 W0 = ldc(Pc + o_w0), WXM = ldc(Pm + o_w0), WXP = ldc(Pn + o_w0);
-        const FF2 U0 = ldc(Pc);
-        const FF2 WYM = ldc(Pc + o_wm), VYM = ldc(Pc + o_vm), WYP = ldc(Pc + o_wp), V0 = ldc(Pc + o_v0);
-        const FF2 wzm = zm(W0, below(W0)), wzp = zp(W0, above<false>(W0, top));
+        const FF2 W0 = ldc(Pc + o_w0);
+        const FF2 U0 = ldc(Pc), V0 = ldc(Pc + o_v0);
+        const FF2 wu_hi = add(W0, ldc(Pn + o_w0));
+        const FF2 wv_hi = add(W0, ldc(Pc + o_wp));
+        const FF2 wzp = zp(W0, above<false>(W0, top));
         const FF2 ww_hi = add(W0, wzp);
-        const FF2 ww_lo = zm(ww_hi, below(ww_hi));
-        const FF2 uzp = zp(U0, above<true>(U0, top)), vzp = zp(V0, above<true>(V0, top));
-        const FF2 fw = add(U0, uzp);
-        const FF2 xw = sub(mul(WXM, FW), mul(WXP, fw));
-        FW = fw;
-        const FF2 yw = sub(mul(WYM, add(VYM, zp(VYM, above<false>(VYM, top)))), mul(WYP, add(V0, vzp)));
-        FF2 hw = add(mul(ldc(a_tc), xw), mul(ldc(a_tc + 16), yw));
-        hw = add(hw, mul(mul(ldc(a_c1 + 32 * KB), wzm), ww_lo));
+        const FF2 wu_lo = zm(wu_hi, below(wu_hi)), wv_lo = zm(wv_hi, below(wv_hi)), ww_lo = zm(ww_hi, below(ww_hi));
+        const FF2 c1 = ldc(a_c1), c2 = ldc(a_c1 + 16 * KB);
+        hu = add(hu, mul(mul(c1, zm(U0, below(U0))), wu_lo));
+        hv = add(hv, mul(mul(c1, zm(V0, below(V0))), wv_lo));
+        hw = add(hw, mul(mul(ldc(a_c1 + 32 * KB), zm(W0, below(W0))), ww_lo));
+        hu = sub(hu, mul(mul(c2, zp(U0, above<true>(U0, top))), wu_hi));
+        hv = sub(hv, mul(mul(c2, zp(V0, above<true>(V0, top))), wv_hi));
         hw = sub(hw, mul(mul(ldc(a_c1 + 48 * KB), wzp), ww_hi));
-        if (row_ok) {  // sw at levels 0 and nz-1 is zero
-          const double w0 = bottom ? 0.0 : assemble(hw.hi.x, hw.lo.x);
-          const double w1 = top ? 0.0 : assemble(hw.hi.y, hw.lo.y);
-          __stcs(reinterpret_cast<double2*>(t.o[2]) + o / 2, make_double2(w0, w1));
-        }
+      }
+      if (row_ok) {
+        // su, sv at level 0 and sw at levels 0 and nz-1 are zero
+        const double u0 = bottom ? 0.0 : assemble(hu.hi.x, hu.lo.x), u1 = assemble(hu.hi.y, hu.lo.y);
+        const double v0 = bottom ? 0.0 : assemble(hv.hi.x, hv.lo.x), v1 = assemble(hv.hi.y, hv.lo.y);
+        const double w0 = bottom ? 0.0 : assemble(hw.hi.x, hw.lo.x);
+        const double w1 = top ? 0.0 : assemble(hw.hi.y, hw.lo.y);
+        __stcs(reinterpret_cast<double2*>(t.o[0]) + o / 2, make_double2(u0, u1));
+        __stcs(reinterpret_cast<double2*>(t.o[1]) + o / 2, make_double2(v0, v1));
+        __stcs(reinterpret_cast<double2*>(t.o[2]) + o / 2, make_double2(w0, w1));
       }
       // plane i-1 is no longer read by this warp
       release(i - t.i_lo, pm);
