@@ -23,12 +23,12 @@
 //    split constants (vertical coefficients, tcx, tcy) sit in a shared table.
 //    Only the three x-face sums a plane shares with the next (u(i) + u(i+1),
 //    u + u(y+1), u + u(z+1) of plane i are plane i+1's x-1 faces) are carried.
+//    That fits the code in 128 registers without spills, so two CTAs of
+//    seven compute warps and the converter run per SM.
 //  * The three source terms are evaluated side by side, stage by stage (x
 //    faces of su, sv, sw, then their y faces, then the vertical faces): the
 //    double-float chains of one term depend on each other, the three terms
 //    do not, so each warp has three independent chains in flight.
-//    That fits the code in 128 registers without spills, so two CTAs of
-//    seven compute warps and the converter run per SM.
 //
 // Double-float sums are TwoSum of the high parts with the low parts added,
 // products the exact product of the high parts (FMA) plus the two cross
@@ -94,7 +94,6 @@ __device__ __forceinline__ FF2 zm(const FF2& v, const F1& below) {
 __device__ __forceinline__ FF2 zp(const FF2& v, const F1& above) {
   return FF2{make_float2(v.hi.y, above.hi), make_float2(v.lo.y, above.lo)};
 }
-
 
 // Vertical halos from the neighbouring lanes (rows do not straddle warps).
 __device__ __forceinline__ F1 below(const FF2& v) {
