@@ -140,15 +140,16 @@ __device__ __forceinline__ FF2 coef2(const double* tab, int k) {
 
 __device__ __forceinline__ FF2 bcast(const ff& x) { return FF2{make_float2(x.hi, x.hi), make_float2(x.lo, x.lo)}; }
 
-// A binary32 value as binary64 by integer bit operations (exact: the
-// exponent rebiased from 127 to 1023, the significand shifted into place);
-// zero and binary32 subnormals (below 2^-126) as a signed zero; infinities
-// and NaN lie outside the double-float mode's range (as for the split).
+// A binary32 value as binary64 by integer bit operations (exact for normal
+// values: the exponent rebiased from 127 to 1023, the significand shifted
+// into place); a signed zero stays exact, binary32 subnormals (below 2^-126)
+// come out below 2^-1000; infinities and NaN lie outside the double-float
+// mode's range (as for the split).
 __device__ __forceinline__ double widen(float x) {
   const uint32_t b = __float_as_uint(x);
-  const uint32_t mag = b & 0x7fffffffu, sign = b & 0x80000000u;
-  const bool zero = mag < 0x00800000u;
-  return __hiloint2double((int)(zero ? sign : (((mag >> 3) + 0x38000000u) | sign)), (int)(zero ? 0u : b << 29));
+  const uint32_t mag = b & 0x7fffffffu;
+  const uint32_t bias = mag >= 0x00800000u ? 0x38000000u : 0u;
+  return __hiloint2double((int)(((mag >> 3) + bias) | (b & 0x80000000u)), (int)(b << 29));
 }
 
 // (hi, lo) of one level -> binary64, rounded once: both parts widened by
